@@ -1,0 +1,273 @@
+// Code generation (Sec. 3.3: the GPU backend emits CUDA for every fused
+// scope): each fused group becomes one hand-written skeleton from kernels/
+// specialised with the group's expression DAG, stencil weights, tile shape
+// and boundary rule.  The expression is emitted as straight-line code in
+// registers; constants are emitted bit-exactly.
+#include <cinttypes>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+
+#include "dcp_internal.h"
+
+namespace dcp {
+
+namespace {
+
+std::string var(int v) { return "v" + std::to_string(v); }
+
+std::string imm_literal(int dtype, double imm) {
+  char buf[96];
+  switch (dtype) {
+    case DCP_F32: {
+      float f = (float)imm;
+      uint32_t b;
+      std::memcpy(&b, &f, 4);
+      std::snprintf(buf, sizeof buf, "__int_as_float(0x%08" PRIx32 ")", b);
+      break;
+    }
+    case DCP_F64: {
+      uint64_t b;
+      std::memcpy(&b, &imm, 8);
+      std::snprintf(buf, sizeof buf, "__longlong_as_double(0x%016" PRIx64 "ll)", b);
+      break;
+    }
+    case DCP_I32: {
+      int64_t i = (int64_t)imm;
+      uint32_t b = (uint32_t)(uint64_t)i;
+      std::snprintf(buf, sizeof buf, "((int)0x%08" PRIx32 "u)", b);
+      break;
+    }
+    default: {
+      int64_t i = (int64_t)imm;
+      std::snprintf(buf, sizeof buf, "((long long)0x%016" PRIx64 "ull)", (uint64_t)i);
+      break;
+    }
+  }
+  return buf;
+}
+
+// Weight literal in the group's dtype (stencils are floating).
+std::string weight_literal(int dtype, double w) { return imm_literal(dtype, w); }
+
+// C expression of map node v applied to operand expressions.
+std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std::string& b) {
+  const Node& n = g.nodes[v];
+  if (n.kind == Kind::Stencil) return a;  // zero-step stencil: identity
+  std::string imm = imm_literal(n.dtype, n.imm);
+  switch (n.op) {
+    case DCP_NEG: return "dcp_neg(" + a + ")";
+    case DCP_ABS: return "dcp_abs(" + a + ")";
+    case DCP_EXP: return "dcp_exp(" + a + ")";
+    case DCP_SIN: return "dcp_sin(" + a + ")";
+    case DCP_COS: return "dcp_cos(" + a + ")";
+    case DCP_TANH: return "dcp_tanh(" + a + ")";
+    case DCP_SQRT: return "dcp_sqrt(" + a + ")";
+    case DCP_SQUARE: return "dcp_square(" + a + ")";
+    case DCP_ADD: return "dcp_add(" + a + ", " + b + ")";
+    case DCP_SUB: return "dcp_sub(" + a + ", " + b + ")";
+    case DCP_MUL: return "dcp_mul(" + a + ", " + b + ")";
+    case DCP_DIV: return "dcp_div(" + a + ", " + b + ")";
+    case DCP_MAX: return "dcp_max(" + a + ", " + b + ")";
+    case DCP_MIN: return "dcp_min(" + a + ", " + b + ")";
+    case DCP_ADD_S: return "dcp_add(" + a + ", " + imm + ")";
+    case DCP_MUL_S: return "dcp_mul(" + a + ", " + imm + ")";
+    case DCP_SUB_S: return "dcp_sub(" + a + ", " + imm + ")";
+    case DCP_RSUB_S: return "dcp_sub(" + imm + ", " + a + ")";
+  }
+  fail(DCP_E_INVALID_ARG, "codegen: unknown op");
+}
+
+void emit_members(std::ostringstream& os, const GraphImpl& g, const std::vector<int>& members) {
+  for (int v : members) {
+    const Node& n = g.nodes[v];
+    std::string a = var(n.in[0]);
+    std::string b = n.in.size() > 1 ? var(n.in[1]) : "";
+    os << "  const DCP_T " << var(v) << " = " << map_expr(g, v, a, b) << ";\n";
+  }
+}
+
+std::string red_op_fn(const GraphImpl& g, const std::vector<int>& reds) {
+  std::ostringstream os;
+  os << "__device__ __forceinline__ constexpr int dcp_red_op(int r) { return ";
+  for (size_t i = 0; i < reds.size(); ++i) os << "r == " << i << " ? " << g.nodes[reds[i]].op << " : ";
+  os << "0; }\n";
+  return os.str();
+}
+
+std::string finish(const std::string& prefix, const std::string& body) {
+  char name[64];
+  std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(), fnv1a(body));
+  return std::string("#define DCP_KNAME ") + name + "\n" + body;
+}
+
+std::string kname_of(const std::string& src) {
+  const char* p = std::strstr(src.c_str(), "#define DCP_KNAME ");
+  std::string s(p + std::strlen("#define DCP_KNAME "));
+  return s.substr(0, s.find('\n'));
+}
+
+}  // namespace
+
+CodegenOut gen_map_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
+  std::ostringstream os;
+  const int T = G.dtype;
+  int vec = vec_ok ? 16 / dtype_size(T) : 1;
+  os << "// dcp fused map kernel: " << G.members.size() << " ops, " << G.loads.size() << " loads, "
+     << G.stores.size() << " stores, " << G.reds.size() << " reductions\n";
+  os << "#define DCP_T " << dtype_cname(T) << "\n";
+  os << "#define DCP_VEC " << vec << "\n#define DCP_UNROLL " << (vec > 1 ? 2 : 1) << "\n";
+  os << "#define DCP_NLOAD " << G.loads.size() << "\n#define DCP_NSTORE " << G.stores.size()
+     << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n#define DCP_NRED " << G.reds.size()
+     << "\n#define DCP_THREADS " << G.threads << "\n";
+  os << red_op_fn(g, G.reds);
+  os << "#include \"dcp_device.cuh\"\n";
+  os << "__device__ __forceinline__ void dcp_body(const DCP_T* ld, const DCP_T* sc, DCP_T* st, "
+        "DCP_T* rv) {\n";
+  for (size_t i = 0; i < G.loads.size(); ++i)
+    os << "  const DCP_T " << var(G.loads[i]) << " = ld[" << i << "];\n";
+  for (size_t i = 0; i < G.scalars.size(); ++i)
+    os << "  const DCP_T " << var(G.scalars[i]) << " = sc[" << i << "];\n";
+  emit_members(os, g, G.members);
+  for (size_t i = 0; i < G.stores.size(); ++i) os << "  st[" << i << "] = " << var(G.stores[i]) << ";\n";
+  for (size_t i = 0; i < G.reds.size(); ++i)
+    os << "  rv[" << i << "] = " << var(g.nodes[G.reds[i]].in[0]) << ";\n";
+  os << "  (void)ld; (void)sc; (void)st; (void)rv;\n}\n";
+  os << "#include \"k_map.cuh\"\n";
+  CodegenOut out;
+  out.source = finish(vec > 1 ? "dcp_map_v" : "dcp_map_s", os.str());
+  out.name = kname_of(out.source);
+  out.threads = G.threads;
+  out.smem_bytes = 0;
+  return out;
+}
+
+namespace {
+
+// Functions shared by 2-D and 3-D stencil sources: input (prologue), post.
+void emit_stencil_io(std::ostringstream& os, const GraphImpl& g, const Group& G, bool first,
+                     bool last) {
+  os << "__device__ __forceinline__ DCP_T dcp_input(const DcpStParamsT<DCP_T>& p, const DCP_T* sc, "
+        "long long gi) {\n";
+  if (first && !G.members.empty()) {
+    for (size_t i = 0; i < G.loads.size(); ++i)
+      os << "  const DCP_T " << var(G.loads[i]) << " = p.ld[" << i << "][gi];\n";
+    emit_members(os, g, G.members);
+    os << "  (void)sc;\n  return " << var(G.st_in) << ";\n}\n";
+  } else {
+    os << "  (void)sc;\n  return p.ld[0][gi];\n}\n";
+  }
+  os << "__device__ __forceinline__ void dcp_post(const DcpStParamsT<DCP_T>& p, const DCP_T* sc, "
+        "long long gi, DCP_T v, DCP_T* st, DCP_T* rv) {\n";
+  if (last) {
+    os << "  const DCP_T " << var(G.st_out) << " = v;\n";
+    for (size_t i = 0; i < G.post_loads.size(); ++i)
+      os << "  const DCP_T " << var(G.post_loads[i]) << " = p.pld[" << i << "][gi];\n";
+    for (size_t i = 0; i < G.scalars.size(); ++i)
+      os << "  const DCP_T " << var(G.scalars[i]) << " = sc[" << i << "];\n";
+    emit_members(os, g, G.post);
+    for (size_t i = 0; i < G.stores.size(); ++i)
+      os << "  st[" << i << "] = " << var(G.stores[i]) << ";\n";
+    for (size_t i = 0; i < G.reds.size(); ++i)
+      os << "  rv[" << i << "] = " << var(g.nodes[G.reds[i]].in[0]) << ";\n";
+  }
+  os << "  (void)p; (void)sc; (void)gi; (void)v; (void)st; (void)rv;\n}\n";
+}
+
+// Epilogue chain of one step as a function of the weighted sum.
+std::string epi_body(const GraphImpl& g, const StepDesc& s) {
+  std::ostringstream os;
+  std::string cur = "v";
+  int k = 0;
+  for (int e : s.epi) {
+    std::string nv = "e" + std::to_string(k++);
+    os << "  const DCP_T " << nv << " = " << map_expr(g, e, cur, "") << ";\n";
+    cur = nv;
+  }
+  os << "  return " << cur << ";\n";
+  return os.str();
+}
+
+}  // namespace
+
+CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
+  const bool batch = G.kind == GroupKind::Batch;
+  const int nd = batch ? 2 : (int)G.shape.size();
+  const int T = G.dtype;
+  const int nsteps = s1 - s0;
+  const bool first = s0 == 0, last = s1 == (int)G.steps.size();
+  std::ostringstream os;
+  os << "// dcp stencil kernel: steps [" << s0 << ", " << s1 << ") of " << G.steps.size()
+     << ", bc " << G.bc << ", " << nd << "-D" << (batch ? ", batched" : "") << "\n";
+  os << "#define DCP_T " << dtype_cname(T) << "\n";
+  os << "#define DCP_THREADS " << G.threads << "\n#define DCP_BC " << G.bc << "\n";
+  os << "#define DCP_LAST " << (last ? 1 : 0) << "\n#define DCP_BATCH " << (batch ? 1 : 0) << "\n";
+  int nstore = last ? (int)G.stores.size() : 1;
+  int nred = last ? (int)G.reds.size() : 0;
+  os << "#define DCP_NSTORE " << nstore << "\n#define DCP_NRED " << nred << "\n#define DCP_NSCALAR "
+     << G.scalars.size() << "\n";
+  os << red_op_fn(g, last ? G.reds : std::vector<int>{});
+  os << "#include \"dcp_device.cuh\"\n";
+  CodegenOut out;
+  out.threads = G.threads;
+  const int rz = G.radius[0], ry = G.radius[1], rx = G.radius[2];
+  if (nd <= 2) {
+    const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
+    const int RY = nd == 1 ? 0 : ry;
+    const int PW = TX + 2 * nsteps * rx, PH = TY + 2 * nsteps * RY;
+    os << "#define DCP_TX " << TX << "\n#define DCP_TY " << TY << "\n#define DCP_RX " << rx
+       << "\n#define DCP_RY " << RY << "\n#define DCP_NSTEPS " << nsteps << "\n";
+    if (!batch) emit_stencil_io(os, g, G, first, last);
+    os << "template <int S> __device__ __forceinline__ DCP_T dcp_sum(const DCP_T* A, int c);\n";
+    os << "template <int S> __device__ __forceinline__ DCP_T dcp_epi(DCP_T v);\n";
+    for (int s = 0; s < nsteps; ++s) {
+      const StepDesc& sd = G.steps[s0 + s];
+      const Node& sn = g.nodes[sd.node];
+      os << "template <> __device__ __forceinline__ DCP_T dcp_sum<" << s
+         << ">(const DCP_T* A, int c) {\n";
+      for (int k = 0; k < sn.npts(); ++k) {
+        int dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+        int off = dy * PW + dx;
+        std::string term = weight_literal(T, sn.weights[k]) + " * A[c + (" + std::to_string(off) + ")]";
+        if (k == 0) os << "  DCP_T acc = " << term << ";\n";
+        else os << "  acc = acc + " << term << ";\n";
+      }
+      os << "  return acc;\n}\n";
+      os << "template <> __device__ __forceinline__ DCP_T dcp_epi<" << s << ">(DCP_T v) {\n"
+         << epi_body(g, sd) << "}\n";
+    }
+    os << "#include \"k_stencil2d.cuh\"\n";
+    out.smem_bytes = 2 * PW * PH * dtype_size(T);
+  } else {
+    if (nsteps != 1) fail(DCP_E_UNSUPPORTED, "3-D stencil launches run one step each");
+    const int TX = G.tile[2], TY = G.tile[1], TZ = G.tile[0];
+    const int PW = TX + 2 * rx, PH = TY + 2 * ry;
+    os << "#define DCP_TX " << TX << "\n#define DCP_TY " << TY << "\n#define DCP_TZ " << TZ
+       << "\n#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_RZ " << rz
+       << "\n";
+    emit_stencil_io(os, g, G, first, last);
+    const StepDesc& sd = G.steps[s0];
+    const Node& sn = g.nodes[sd.node];
+    os << "__device__ __forceinline__ DCP_T dcp_sum3(const DCP_T* const* pl, int c) {\n";
+    for (int k = 0; k < sn.npts(); ++k) {
+      int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+      std::string term = weight_literal(T, sn.weights[k]) + " * pl[" + std::to_string(dz + rz) +
+                         "][c + (" + std::to_string(dy * PW + dx) + ")]";
+      if (k == 0) os << "  DCP_T acc = " << term << ";\n";
+      else os << "  acc = acc + " << term << ";\n";
+    }
+    os << "  return acc;\n}\n";
+    os << "__device__ __forceinline__ DCP_T dcp_epi3(DCP_T v) {\n" << epi_body(g, sd) << "}\n";
+    os << "#include \"k_stencil3d.cuh\"\n";
+    out.smem_bytes = (2 * rz + 1) * PW * PH * dtype_size(T);
+  }
+  out.source = finish(batch ? "dcp_batch" : (nd == 3 ? "dcp_st3d" : "dcp_st2d"), os.str());
+  out.name = kname_of(out.source);
+  return out;
+}
+
+CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
+  return gen_stencil_kernel(g, G, s0, s1);
+}
+
+}  // namespace dcp

@@ -1,0 +1,211 @@
+// Internal declarations of the dcp runtime: graph IR, fused plan, codegen,
+// run-time compilation and execution.  Not part of the public ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dcp.h"
+
+namespace dcp {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws dcp::Error; the C ABI layer converts it into a
+// status code plus the thread-local message.
+// ---------------------------------------------------------------------------
+struct Error {
+  dcp_status code;
+  std::string msg;
+};
+[[noreturn]] void fail(dcp_status code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+void check_cu(CUresult r, const char* what);
+
+// Driver API entry points (driver.cpp), resolved through the runtime.
+struct Driver {
+  CUresult (*ctxGetCurrent)(CUcontext*) = nullptr;
+  CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
+  CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
+  CUresult (*funcGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;
+  CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+  CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
+  CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                           unsigned, CUstream, void**, void**) = nullptr;
+  CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+};
+const Driver& drv();
+
+int dtype_size(int dtype);
+bool dtype_is_float(int dtype);
+const char* dtype_cname(int dtype);  // C type used in generated code
+const char* dtype_name(int dtype);
+
+// ---------------------------------------------------------------------------
+// Graph IR: one node per NumPy-level operation (SSA form, Sec. 2.3).
+// ---------------------------------------------------------------------------
+enum class Kind { Input, Map, Stencil, Reduce };
+
+struct Node {
+  Kind kind = Kind::Input;
+  int dtype = DCP_F32;
+  std::vector<int64_t> shape;
+  int op = -1;              // map op / reduce op
+  std::vector<int> in;      // operand value ids
+  double imm = 0.0;
+  // stencil
+  std::vector<int32_t> offsets;  // npts * ndim
+  std::vector<double> weights;
+  int bc = DCP_BC_ZERO;
+  int steps = 0;
+  int64_t numel() const {
+    int64_t n = 1;
+    for (auto s : shape) n *= s;
+    return n;
+  }
+  int ndim() const { return (int)shape.size(); }
+  int npts() const { return (int)weights.size(); }
+};
+
+bool op_is_unary(int op);
+bool op_is_binary(int op);
+bool op_is_scalar_imm(int op);
+bool op_float_only(int op);
+const char* op_name(int op);
+const char* red_name(int red);
+
+// ---------------------------------------------------------------------------
+// Fused plan (Sec. 3.1: greedy subgraph fusion, tiled write-conflict
+// resolution, transient mitigation).
+// ---------------------------------------------------------------------------
+enum class GroupKind { Map, Stencil, Batch };
+
+// One step of an iterated stencil inside a stencil group.  `node` is the
+// stencil node providing offsets/weights; `epi` the unary/immediate map nodes
+// applied, in order, to the weighted sum (stencil -> map epilogue fusion).
+struct StepDesc {
+  int node = -1;
+  std::vector<int> epi;
+};
+
+struct Group {
+  GroupKind kind = GroupKind::Map;
+  int dtype = DCP_F32;
+  std::vector<int64_t> shape;   // iteration space
+  // Map groups: members computed in registers, in topological order.
+  // Stencil groups: prologue members producing `st_in` (may be empty, then
+  // st_in is loaded), steps, then post members computed from `st_out`.
+  std::vector<int> members;     // map node ids (map groups) / prologue members
+  std::vector<int> post;        // post members (stencil groups)
+  std::vector<int> loads;       // full-shape values read from memory (map / prologue)
+  std::vector<int> post_loads;  // full-shape values read at the output index (stencil post)
+  std::vector<int> scalars;     // 0-axis values broadcast into the expressions
+  std::vector<int> stores;      // values written to memory by this group
+  std::vector<int> reds;        // reduce node ids computed here
+  int st_in = -1;               // stencil input value
+  int st_out = -1;              // value after the last step (+ its epilogue)
+  std::vector<StepDesc> steps;
+  int bc = DCP_BC_ZERO;
+  std::vector<int32_t> offsets;  // common offset set, padded to 3 axes (dz,dy,dx)
+  int radius[3] = {0, 0, 0};
+  // launch decomposition
+  int depth = 1;                // stencil steps per launch
+  int tile[3] = {1, 1, 1};      // output tile (z, y, x) for stencils
+  int threads = 256;
+  int blocks_per_sm = 4;
+  // batch groups: the member stencil groups (same program, different shapes)
+  std::vector<int> batch_members;  // indices into Plan::groups of absorbed groups
+  bool absorbed = false;           // this stencil group runs inside a batch group
+};
+
+struct Kernel {
+  std::string name;
+  std::string source;
+  CUfunction fn = nullptr;
+  int smem_bytes = 0;
+  int threads = 256;
+  double compile_ms = 0.0;
+  int regs = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Run-time compilation (NVRTC -> cubin for sm_103a, Sec. 3.3) and a module
+// cache keyed by the source text.
+// ---------------------------------------------------------------------------
+struct CompiledModule {
+  CUmodule mod = nullptr;
+  std::vector<char> cubin;
+  double compile_ms = 0.0;
+  bool from_cache = false;
+};
+std::vector<char> nvrtc_compile(const std::string& src, const std::string& name, double* ms,
+                                std::string* log);
+CUfunction load_function(const std::string& src, const std::string& name, double* ms, int* regs);
+const char* device_header_source();     // dcp_device.cuh
+const char* kernel_map_source();        // k_map.cuh
+const char* kernel_stencil2d_source();  // k_stencil2d.cuh
+const char* kernel_stencil3d_source();  // k_stencil3d.cuh
+const char* kernel_adjoint_source();    // k_adjoint.cuh
+
+// ---------------------------------------------------------------------------
+// Graph object
+// ---------------------------------------------------------------------------
+struct LaunchRec;  // defined in runtime.cpp
+
+struct GraphImpl {
+  std::vector<Node> nodes;
+  std::vector<int> inputs;
+  std::vector<int> outputs;
+  bool fused = false;
+  uint32_t flags = 0;
+  std::map<int, int64_t> options;
+  std::vector<Group> groups;      // in execution order
+  std::vector<Group> batch_store; // stencil groups packed into batch groups
+  std::vector<int> value_group;   // value id -> producing group (-1 input)
+  std::vector<char> materialized; // value id -> needs a device buffer
+  int n_launches = 0;
+  std::string plan_json;
+  // runtime state (runtime.cpp)
+  struct Runtime;
+  std::unique_ptr<Runtime> rt;
+  GraphImpl();
+  ~GraphImpl();
+};
+
+void plan_graph(GraphImpl& g, uint32_t flags);      // fuse.cpp
+void compile_plan(GraphImpl& g);                    // runtime.cpp
+void run_graph(GraphImpl& g, const void* const* inputs, void* const* outputs, cudaStream_t s);
+void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* outputs,
+                    cudaStream_t s);
+void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out_grads,
+                 void* const* in_grads, size_t budget, cudaStream_t s);
+void sync_graph(GraphImpl& g, cudaStream_t s);
+std::string describe_plan(const GraphImpl& g);
+
+// codegen.cpp
+struct CodegenOut {
+  std::string name;
+  std::string source;
+  int smem_bytes = 0;
+  int threads = 256;
+};
+CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
+// Stencil launch `chunk` covers steps [s0, s1) of the group.
+CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
+CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
+// adjoint kernels
+CodegenOut gen_map_adjoint_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
+CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int step);
+
+uint64_t fnv1a(const std::string& s);
+
+constexpr int kMaxIO = 16;       // loads / stores / reductions per kernel
+constexpr int kMaxRadius = 4;
+constexpr int kMaxPoints = 32;
+
+}  // namespace dcp

@@ -1,0 +1,191 @@
+"""C ABI checks that need no GPU: the library loads and exports every symbol
+include/dcp.h declares, the builder rejects malformed programs with the
+documented status codes, and the planner fuses programs into the expected
+kernels (plan structure), compiling every generated kernel for sm_103a."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2107_00555_gb300 import DcpError, Graph, programs
+from paper_2107_00555_gb300 import _capi as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "dcp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dcp_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(C.lib_path())
+    names = _header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(C.EXPORTED), set(names) - set(C.EXPORTED)
+
+
+def _err(fn, *args):
+    with pytest.raises(DcpError) as e:
+        fn(*args)
+    return e.value.status
+
+
+def test_builder_validation():
+    g = Graph()
+    x = g.input("f32", (10,))
+    y = g.input("f64", (10,))
+    z = g.input("f32", (11,))
+    i = g.input("i32", (10,))
+    s = g.input("f32", ())
+    assert _err(g.map, "add", [x, y]) == C.DCP_E_DTYPE
+    assert _err(g.map, "add", [x, z]) == C.DCP_E_SHAPE
+    assert _err(g.map, "exp", [i]) == C.DCP_E_DTYPE
+    assert _err(g.map, "div", [i, i]) == C.DCP_E_DTYPE
+    assert _err(g.map, 99, [x]) == C.DCP_E_INVALID_ARG
+    assert _err(g.map, "add", [x]) == C.DCP_E_INVALID_ARG
+    assert _err(g.map, "add_s", [i], 0.5) == C.DCP_E_INVALID_ARG
+    assert _err(g.map, "neg", [12345]) == C.DCP_E_INVALID_ARG
+    assert _err(g.stencil, i, [(0,)], [1.0]) == C.DCP_E_DTYPE
+    assert _err(g.stencil, x, [(5,)], [1.0]) == C.DCP_E_INVALID_ARG
+    assert _err(g.stencil, s, [(0,)], [1.0]) == C.DCP_E_SHAPE
+    assert _err(g.stencil, x, [(0,)], [1.0], 7) == C.DCP_E_INVALID_ARG
+    e = g.input("f64", (0,))
+    assert _err(g.reduce, e, "max") == C.DCP_E_SHAPE
+    g.reduce(e, "sum")  # sum of empty is 0
+    assert _err(g.output, x) == C.DCP_E_INVALID_ARG  # inputs cannot be outputs
+    v = g.map("add", [x, s])  # 0-axis operand broadcasts
+    assert g.shape[v] == (10,)
+    assert _err(g.fuse, 0) == C.DCP_E_STATE  # no outputs yet
+    g.output(v)
+    assert _err(g.output, v) == C.DCP_E_INVALID_ARG
+    assert g.fuse(C.DCP_FUSE_ALL) == 1
+    assert _err(g.map, "neg", [x]) == C.DCP_E_STATE
+    assert _err(g.fuse, 0) == C.DCP_E_STATE
+    assert _err(C.dcp_fuse, g._h, 1 << 20) == C.DCP_E_STATE
+
+
+def test_unknown_fuse_flag_and_options():
+    g = Graph()
+    x = g.input("f32", (4,))
+    g.output(g.map("neg", [x]))
+    assert _err(C.dcp_fuse, g._h, 1 << 20) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, 999, 1) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, C.DCP_OPT_TIME_TILE_DEPTH, 0) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, C.DCP_OPT_TILE_X, 12) == C.DCP_E_INVALID_ARG
+    g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 3)
+    g.fuse(0)
+    assert _err(g.set_option, C.DCP_OPT_TIME_TILE_DEPTH, 2) == C.DCP_E_STATE
+
+
+def test_null_handles():
+    lib = C.load()
+    assert lib.dcp_add_input(None, 1, 1, None, None) == C.DCP_E_INVALID_ARG
+    assert "NULL" in C.dcp_last_error()
+    assert lib.dcp_graph_destroy(None) == C.DCP_OK
+    assert lib.dcp_run(None, None, None, None) == C.DCP_E_INVALID_ARG
+
+
+def test_plan_map_reduce():
+    g = programs.map_reduce(1 << 20, "f32", fuse=C.DCP_FUSE_ALL)
+    p = g.plan()
+    assert p["n_launches"] == 1 and len(p["groups"]) == 1
+    grp = p["groups"][0]
+    assert grp["members"] == 8 and grp["reductions"] == 2 and grp["stores"] == 0
+    assert grp["loads"] == 3 and p["transient_bytes"] == 0
+    g0 = programs.map_reduce(1 << 20, "f32", fuse=0)
+    p0 = g0.plan()
+    assert p0["n_launches"] == 10
+    # every one of the 8 map temporaries is materialised op by op
+    assert p0["transient_bytes"] == 8 * (1 << 20) * 4
+
+
+def test_plan_maps_only_keeps_reductions_separate():
+    g = programs.map_reduce(1000, "f64", fuse=C.DCP_FUSE_MAPS)
+    p = g.plan()
+    # one fused map kernel storing y, then one kernel per reduction
+    assert p["n_launches"] == 3
+    assert p["transient_bytes"] == 1000 * 8
+
+
+def test_plan_tanh_chain_epilogues_and_loss():
+    g = programs.tanh_chain((16, 16, 16), 5, fuse=C.DCP_FUSE_ALL)
+    p = g.plan()
+    assert len(p["groups"]) == 1
+    grp = p["groups"][0]
+    # 5 tanh epilogues, and the loss's square folds into the last step's epilogue
+    assert grp["kind"] == "stencil" and grp["steps"] == 5 and grp["epilogue_ops"] == 6
+    assert grp["post"] == 0 and grp["reductions"] == 1 and grp["stores"] == 0
+    assert p["n_launches"] == 5 and p["transient_bytes"] == 0
+
+
+def test_plan_prologue_fusion():
+    g = Graph()
+    u = g.input("f64", (64, 64))
+    w = g.input("f64", (64, 64))
+    v = g.map("mul", [g.map("exp", [u]), w])
+    g.output(g.stencil(v, programs.FIVE_POINT, programs.FIVE_WEIGHTS, "periodic", 3))
+    g.fuse(C.DCP_FUSE_ALL)
+    p = g.plan()
+    assert len(p["groups"]) == 1
+    assert p["groups"][0]["members"] == 2 and p["groups"][0]["loads"] == 2
+
+
+def test_plan_time_tile_depth():
+    g = programs.jacobi2d((300, 300), 10, "zero", "f32")
+    g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 4)
+    assert g.fuse(C.DCP_FUSE_ALL) == 3
+    g = programs.jacobi2d((300, 300), 10, "zero", "f32", fuse=C.DCP_FUSE_SUBGRAPH)
+    assert g.n_kernels == 10  # no time tiling without the flag
+
+
+def test_plan_batch():
+    g = programs.batch2d([33, 64, 100, 512], 20, fuse=C.DCP_FUSE_ALL | C.DCP_BATCH)
+    p = g.plan()
+    assert len(p["groups"]) == 1 and p["groups"][0]["kind"] == "batch"
+    assert p["groups"][0]["instances"] == 4
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "i64"])
+def test_every_op_compiles(dtype):
+    g = Graph()
+    a = g.input(dtype, (33,))
+    b = g.input(dtype, (33,))
+    s = g.input(dtype, ())
+    v = a
+    ops = ["neg", "abs", "square", "add", "sub", "mul", "max", "min", "add_s", "mul_s", "sub_s",
+           "rsub_s"]
+    if dtype.startswith("f"):
+        ops += ["exp", "sin", "cos", "tanh", "sqrt", "div"]
+    for op in ops:
+        if op in ("add", "sub", "mul", "max", "min", "div"):
+            v = g.map(op, [v, b])
+        elif op.endswith("_s"):
+            v = g.map(op, [v], 3.0)
+        else:
+            v = g.map(op, [v])
+    v = g.map("add", [v, s])
+    g.output(v)
+    for red in ("sum", "max", "min", "maxabs"):
+        g.output(g.reduce(v, red))
+    assert g.fuse(C.DCP_FUSE_ALL) == 1
+
+
+@pytest.mark.parametrize("bc", ["zero", "periodic", "fixed_ring"])
+@pytest.mark.parametrize("shape", [(50,), (20, 30), (9, 10, 11)])
+def test_stencil_kernels_compile(bc, shape):
+    nd = len(shape)
+    offs = [tuple([0] * nd), tuple([1] + [0] * (nd - 1)), tuple([0] * (nd - 1) + [-2])]
+    for dtype in ("f32", "f64"):
+        g = Graph()
+        u = g.input(dtype, shape)
+        v = g.map("sin", [u])
+        st = g.stencil(v, offs, [0.5, 0.25, 0.25], bc, 3)
+        t = g.map("tanh", [st])
+        g.output(g.reduce(g.map("square", [t]), "sum"))
+        g.output(t)
+        g.fuse(C.DCP_FUSE_ALL)

@@ -1,0 +1,172 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Floating tolerances are the mixed bounds |gpu - ref| <= tol * max(|ref|, s):
+1e-12 (f64) / 1e-5 (f32) for maps and stencils, with s the magnitude scale of
+the computation (for the fused map: |exp(ax+b) sin x| + |0.5 x^2|; for the
+averaging stencils, whose weights are non-negative and sum to 1:
+||u0||_inf); reductions use 1e-10 / 1e-4 times sum|y_i| (the backward-stable
+bound of any summation order).  Integer work is compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import programs as OP
+from paper_2107_00555_gb300 import Graph, inputs, programs
+from paper_2107_00555_gb300 import _capi as C
+
+from gpu_util import assert_close, red_tol_for, tol_for, to_dev, to_host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NP = {"f32": np.float32, "f64": np.float64}
+FUSED = C.DCP_FUSE_ALL
+OPBYOP = 0
+
+
+def _map_reduce_check(dtype, n, flags, seed):
+    x, a, b = inputs.cfg2(NP[dtype], seed=seed, n=n)
+    prog = OP.map_reduce(n)
+    vals, extra = oracle.run(prog, [x, a, b], detail=True)
+    H = prog.handles
+    y = vals[H["y"]]
+    scale = np.abs(vals[H["p"]]) + np.abs(vals[H["h"]])
+    s_id, m_id = prog.outputs
+    g = programs.map_reduce(n, dtype, fuse=flags)
+    out = g.run([to_dev(x), to_dev(a), to_dev(b)])
+    torch.cuda.synchronize()
+    s_gpu, m_gpu = float(to_host(out[0])), float(to_host(out[1]))
+    tol, rtol = tol_for(dtype), red_tol_for(dtype)
+    fs, sa = extra[s_id]["fsum"], extra[s_id]["abs"]
+    assert abs(s_gpu - fs) <= rtol * max(sa, 1e-300), (s_gpu, fs, sa)
+    m_ref = float(vals[m_id])
+    assert abs(m_gpu - m_ref) <= tol * max(float(scale.max()) if n else 0.0, m_ref), (m_gpu, m_ref)
+    return y, scale
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [1, 3, 8, 1000, 4099, (1 << 20) + 5])
+@pytest.mark.parametrize("flags", [FUSED, OPBYOP])
+def test_map_reduce_small(dtype, n, flags):
+    _map_reduce_check(dtype, n, flags, seed=1 + n % 3)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_map_reduce_materialised_y(dtype):
+    """Same program with y also an output: elementwise check of the fused map."""
+    n = 70001
+    x, a, b = inputs.cfg2(NP[dtype], seed=2, n=n)
+    prog = OP.map_reduce(n)
+    vals = oracle.run(prog, [x, a, b])
+    H = prog.handles
+    scale = np.abs(vals[H["p"]]) + np.abs(vals[H["h"]])
+    g = Graph()
+    xv, av, bv = (g.input(dtype, (n,)) for _ in range(3))
+    t = g.map("add", [g.map("mul", [av, xv]), bv])
+    y = g.map("sub", [g.map("mul", [g.map("exp", [t]), g.map("sin", [xv])]),
+                      g.map("mul_s", [g.map("mul", [xv, xv])], 0.5)])
+    g.output(y)
+    g.output(g.reduce(y, "sum"))
+    assert g.fuse(FUSED) == 1
+    out = g.run([to_dev(x), to_dev(a), to_dev(b)])
+    assert_close(to_host(out[0]), vals[H["y"]], tol_for(dtype), scale, "y")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_map_reduce_full_size(dtype):
+    """The benchmark workload: 2**26 elements, every element against the oracle."""
+    n = 1 << 26
+    x, a, b = inputs.cfg2(NP[dtype], n=n)
+    prog = OP.map_reduce(n)
+    vals, extra = oracle.run(prog, [x, a, b], detail=True)
+    H = prog.handles
+    s_id, m_id = prog.outputs
+    g = programs.map_reduce(n, dtype, fuse=FUSED)
+    out = g.run([to_dev(x), to_dev(a), to_dev(b)])
+    torch.cuda.synchronize()
+    fs, sa = extra[s_id]["fsum"], extra[s_id]["abs"]
+    assert abs(float(to_host(out[0])) - fs) <= red_tol_for(dtype) * sa
+    scale = np.abs(vals[H["p"]]) + np.abs(vals[H["h"]])
+    assert abs(float(to_host(out[1])) - float(vals[m_id])) <= tol_for(dtype) * max(
+        float(scale.max()), float(vals[m_id]))
+
+
+def test_reductions_deterministic():
+    n = (1 << 22) + 17
+    x, a, b = inputs.cfg2(np.float32, seed=3, n=n)
+    g = programs.map_reduce(n, "f32", fuse=FUSED)
+    d = [to_dev(x), to_dev(a), to_dev(b)]
+    r1 = [to_host(t).copy() for t in g.run(d)]
+    r2 = [to_host(t).copy() for t in g.run(d)]
+    assert r1[0].tobytes() == r2[0].tobytes() and r1[1].tobytes() == r2[1].tobytes()
+
+
+# ---------------------------------------------------------------------------
+# stencils
+# ---------------------------------------------------------------------------
+
+def _stencil_check(build_dev, build_orc, shape, steps, bc, dtype, flags, seed, depth=None):
+    u0 = inputs.uniform(shape, -1.0, 1.0, seed, NP[dtype])
+    ref = oracle.run(build_orc(shape, steps, bc), [u0])[-1]
+    g = build_dev(shape, steps, bc, dtype)
+    if depth is not None:
+        g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+    g.fuse(flags)
+    out = g.run([to_dev(u0)])
+    s = float(np.max(np.abs(u0))) if u0.size else 0.0
+    assert_close(to_host(out[0]), ref, tol_for(dtype), s, "stencil %s %s %s" % (shape, bc, dtype))
+    return to_host(out[0])
+
+
+@pytest.mark.parametrize("bc", ["zero", "periodic", "fixed_ring"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 7), (37, 45), (64, 200), (256, 256)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_jacobi2d(bc, shape, dtype):
+    for flags, depth in ((FUSED, None), (FUSED, 3), (OPBYOP, None)):
+        _stencil_check(programs.jacobi2d, OP.jacobi2d, shape, 7, bc, dtype, flags, seed=11,
+                       depth=depth)
+
+
+@pytest.mark.parametrize("bc", ["zero", "periodic", "fixed_ring"])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 4, 5), (17, 19, 40), (40, 33, 70)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_heat3d(bc, shape, dtype):
+    for flags in (FUSED, OPBYOP):
+        _stencil_check(programs.heat3d, OP.heat3d, shape, 3, bc, dtype, flags, seed=12)
+
+
+def test_jacobi2d_config1_full():
+    """256 x 256 float64, zero boundary, 10 steps, U[0,1) (the small configuration)."""
+    u0 = inputs.cfg1()
+    ref = oracle.run(OP.jacobi2d((256, 256), 10, "zero"), [u0])[-1]
+    for flags in (FUSED, OPBYOP):
+        g = programs.jacobi2d((256, 256), 10, "zero", "f64", fuse=flags)
+        out = g.run([to_dev(u0)])
+        assert_close(to_host(out[0]), ref, 1e-12, float(u0.max()), "cfg1")
+
+
+def test_time_tiling_is_bit_exact():
+    """k steps per launch give bit-identical results to one step per launch."""
+    u0 = inputs.uniform((300, 257), 0.0, 1.0, 5)
+    res = []
+    for depth in (1, 2, 5):
+        g = programs.jacobi2d((300, 257), 10, "zero", "f64")
+        g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+        g.fuse(FUSED)
+        res.append(to_host(g.run([to_dev(u0)])[0]).copy())
+    assert res[0].tobytes() == res[1].tobytes() == res[2].tobytes()
+
+
+def test_jacobi1d_paper_form():
+    u0 = inputs.uniform((1000,), 0.0, 1.0, 9)
+    offs, w = [(-1,), (0,), (1,)], [0.33333] * 3
+    p = oracle.Program()
+    v = p.input("f64", (1000,))
+    p.output(p.stencil(v, offs, w, "fixed_ring", 12))
+    ref = oracle.run(p, [u0])[-1]
+    g = Graph()
+    v = g.input("f64", (1000,))
+    g.output(g.stencil(v, offs, w, "fixed_ring", 12))
+    g.fuse(FUSED)
+    assert_close(to_host(g.run([to_dev(u0)])[0]), ref, 1e-12, 1.0, "jacobi1d")

@@ -213,11 +213,9 @@ class MapReduce(Workload):
         return self.bytes / dt / GB, "full workload: 2^26 elements, one oracle pass", 1
 
 
-def make_workload(name):
-    if name == "map_reduce_f32":
-        return MapReduce("f32")
-    if name == "map_reduce_f64":
-        return MapReduce("f64")
+def make_workload(name, n=None):
+    if name in ("map_reduce_f32", "map_reduce_f64"):
+        return MapReduce(name[-3:], n or (1 << 26))
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -261,7 +259,7 @@ def run_dcp(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    wl = make_workload(args.workload)
+    wl = make_workload(args.workload, args.n)
     wl.setup(torch, dev)
     stream = torch.cuda.current_stream()
 
@@ -284,6 +282,16 @@ def run_dcp(args):
 
     # comparison forms and roofline (rank-local)
     per_launch = _per_launch(torch, wl.step, max(5, args.steps), stream)
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "workload": wl.name, "elements": wl.n,
+                              "ms_per_step": t / args.steps * 1e3,
+                              "value": world * wl.bytes * args.steps / t / GB,
+                              "per_launch_ms": per_launch * 1e3,
+                              "kernels": wl.kernels}), flush=True)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
     for _ in range(2):
         wl.step_opbyop()
     t_op = _time_device(torch, wl.step_opbyop, max(3, args.steps // 2), stream) / max(3, args.steps // 2)
@@ -402,6 +410,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dcp", choices=["dcp", "reference"])
     ap.add_argument("--workload", default="map_reduce_f32")
+    ap.add_argument("--n", type=int, default=None, help="element count override (profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the fused program only (no comparison legs); for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -56,6 +56,11 @@ std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std:
   if (n.kind == Kind::Stencil) return a;  // zero-step stencil: identity
   std::string imm = imm_literal(n.dtype, n.imm);
   switch (n.op) {
+    case kOpBcast: return a;
+    case kOpConst: return imm;
+    case kOpSign: return "dcp_sign(" + a + ")";
+    case kOpGt: return "dcp_gt(" + a + ", " + b + ")";
+    case kOpLt: return "dcp_lt(" + a + ", " + b + ")";
     case DCP_NEG: return "dcp_neg(" + a + ")";
     case DCP_ABS: return "dcp_abs(" + a + ")";
     case DCP_EXP: return "dcp_exp(" + a + ")";
@@ -81,7 +86,7 @@ std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std:
 void emit_members(std::ostringstream& os, const GraphImpl& g, const std::vector<int>& members) {
   for (int v : members) {
     const Node& n = g.nodes[v];
-    std::string a = var(n.in[0]);
+    std::string a = n.in.empty() ? "" : var(n.in[0]);
     std::string b = n.in.size() > 1 ? var(n.in[1]) : "";
     os << "  const DCP_T " << var(v) << " = " << map_expr(g, v, a, b) << ";\n";
   }
@@ -152,6 +157,8 @@ void emit_stencil_io(std::ostringstream& os, const GraphImpl& g, const Group& G,
   if (first && !G.members.empty()) {
     for (size_t i = 0; i < G.loads.size(); ++i)
       os << "  const DCP_T " << var(G.loads[i]) << " = p.ld[" << i << "][gi];\n";
+    for (size_t i = 0; i < G.scalars.size(); ++i)
+      os << "  const DCP_T " << var(G.scalars[i]) << " = sc[" << i << "];\n";
     emit_members(os, g, G.members);
     os << "  (void)sc;\n  return " << var(G.st_in) << ";\n}\n";
   } else {

@@ -72,6 +72,13 @@ struct Node {
   int npts() const { return (int)weights.size(); }
 };
 
+// Internal map ops (emitted by the adjoint builder only, never by the ABI).
+constexpr int kOpBcast = 100;  // y = 0-axis operand broadcast to the shape
+constexpr int kOpConst = 101;  // y = imm
+constexpr int kOpSign = 102;   // y = sign(x), sign(0) = 0
+constexpr int kOpGt = 103;     // y = a > b ? 1 : 0
+constexpr int kOpLt = 104;     // y = a < b ? 1 : 0
+
 bool op_is_unary(int op);
 bool op_is_binary(int op);
 bool op_is_scalar_imm(int op);
@@ -173,6 +180,7 @@ struct GraphImpl {
   // runtime state (runtime.cpp)
   struct Runtime;
   std::unique_ptr<Runtime> rt;
+  std::shared_ptr<struct AdjointState> adj;  // adjoint.cpp
   GraphImpl();
   ~GraphImpl();
 };
@@ -185,6 +193,12 @@ void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* output
 void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out_grads,
                  void* const* in_grads, size_t budget, cudaStream_t s);
 void sync_graph(GraphImpl& g, cudaStream_t s);
+void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
+                      const void* const* out_grads, void* const* in_grads, size_t budget,
+                      cudaStream_t s);
+std::shared_ptr<AdjointState> new_adjoint_state();
+size_t adjoint_tape_bytes(const AdjointState& st);
+bool adjoint_chunked(const AdjointState& st);
 std::string describe_plan(const GraphImpl& g);
 
 // codegen.cpp

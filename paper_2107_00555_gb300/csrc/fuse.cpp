@@ -144,19 +144,16 @@ struct Planner {
       }
     }
     // (3) no producer group qualifies (e.g. every operand is a program input):
-    //     join the latest map group over the same iteration space whose
-    //     operands are all available when it runs.
-    if (best < 0 && fmaps() && !n.shape.empty()) {
-      for (int gi = (int)g.groups.size() - 1; gi >= 0; --gi) {
-        const Group& G = g.groups[gi];
-        if (G.kind != GroupKind::Map || G.shape != n.shape) continue;
+    //     extend the contiguous subgraph, i.e. join the latest group if it is
+    //     a map group over the same iteration space.
+    if (best < 0 && fmaps() && !n.shape.empty() && !g.groups.empty()) {
+      int gi = (int)g.groups.size() - 1;
+      const Group& G = g.groups[gi];
+      if (G.kind == GroupKind::Map && G.shape == n.shape) {
         bool ok = true;
         for (int b : n.in)
           if (!computed_in(gi, b) && !available_before(b, gi)) ok = false;
-        if (ok) {
-          best = gi;
-          break;
-        }
+        if (ok) best = gi;
       }
     }
     if (best >= 0) {
@@ -253,7 +250,7 @@ struct Planner {
     if (fsub() && gi >= 0 && gi == (int)g.groups.size() - 1 &&
         g.groups[gi].kind == GroupKind::Map && computed_in(gi, a)) {
       Group& M = g.groups[gi];
-      bool ok = M.reds.empty() && M.scalars.empty() && M.shape == n.shape;
+      bool ok = M.reds.empty() && M.shape == n.shape;
       for (int m : M.members) {
         if (is_out[m]) ok = false;
         for (int u : users[m])
@@ -263,6 +260,7 @@ struct Planner {
       if (ok) {
         S.members = M.members;
         S.loads = M.loads;
+        S.scalars = M.scalars;
         g.groups.pop_back();
       }
     }

@@ -62,6 +62,11 @@ __device__ __forceinline__ float dcp_div(float a, float b) { return a / b; }
 __device__ __forceinline__ double dcp_div(double a, double b) { return a / b; }
 
 template <typename T> __device__ __forceinline__ T dcp_square(T a) { return dcp_mul(a, a); }
+template <typename T> __device__ __forceinline__ T dcp_sign(T a) {
+  return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
+}
+template <typename T> __device__ __forceinline__ T dcp_gt(T a, T b) { return a > b ? (T)1 : (T)0; }
+template <typename T> __device__ __forceinline__ T dcp_lt(T a, T b) { return a < b ? (T)1 : (T)0; }
 
 __device__ __forceinline__ float dcp_exp(float a) { return expf(a); }
 __device__ __forceinline__ double dcp_exp(double a) { return exp(a); }

@@ -57,6 +57,7 @@ struct LaunchSpec {
   double compile_ms = 0.0;
   int regs = 0;
   int occupancy = 0;
+  int occ_scalar = 1;
 };
 
 int64_t numel(const std::vector<int64_t>& s) {
@@ -293,16 +294,20 @@ static void launch_map(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
   if (p.n == 0 && G.reds.empty()) return;
   CUfunction fn = ls.fn;
   int per = 16 / (int)esz;
+  int occ = ls.occupancy;
   if (!vec) {
     if (!ls.fn_scalar) {
       ls.fn_scalar = load_function(ls.code_scalar.source, ls.code_scalar.name, nullptr, nullptr);
+      check_cu(drv().occupancy(&ls.occ_scalar, ls.fn_scalar, G.threads, 0), "occupancy query");
     }
     fn = ls.fn_scalar;
     per = 1;
+    occ = ls.occ_scalar;
   }
+  // one wave of resident CTAs (grid-stride loop): no partial second wave
   int64_t work = (p.n + per - 1) / per;
   int64_t blocks = (work + G.threads - 1) / G.threads;
-  int64_t maxb = (int64_t)rt.sms * G.blocks_per_sm;
+  int64_t maxb = (int64_t)rt.sms * std::max(1, std::min(G.blocks_per_sm, occ));
   if (blocks > maxb) blocks = maxb;
   if (blocks < 1) blocks = 1;
   void* args[] = {&p};
@@ -574,8 +579,9 @@ std::string describe_plan(const GraphImpl& g) {
 
 void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out_grads,
                  void* const* in_grads, size_t budget, cudaStream_t s) {
-  (void)g; (void)inputs; (void)out_grads; (void)in_grads; (void)budget; (void)s;
-  fail(DCP_E_UNSUPPORTED, "adjoint not available in this build");
+  ensure_device(g);
+  if (!g.adj) g.adj = new_adjoint_state();
+  run_adjoint_impl(g, *g.adj, inputs, out_grads, in_grads, budget, s);
 }
 
 }  // namespace dcp

@@ -142,6 +142,10 @@ class Workload:
     def step(self):
         raise NotImplementedError
 
+    def value(self, t_step):
+        """Metric value for one step taking t_step seconds."""
+        return self.bytes / t_step / GB
+
 
 def _np_dtype(d):
     import numpy as np
@@ -154,6 +158,11 @@ class MapReduce(Workload):
         self.n = n
         self.name = "map_reduce_%s" % dtype
         self.bytes = 3 * n * (4 if dtype == "f32" else 8)
+
+    def roof(self):
+        # f32: device memory bound (3 arrays read once); f64: the FP64 ALUs (exp and
+        # sin in binary64); counted as HBM work here, see the design notes
+        return "hbm", self.bytes, "bytes"
 
     def describe(self):
         return {"workload": "fused map+reduce: y = exp(a*x+b)*sin(x) - 0.5*x*x; sum(y), max|y|",
@@ -180,6 +189,9 @@ class MapReduce(Workload):
 
     def step_opbyop(self):
         self.g0.run(self.dev, self.out0)
+
+    def legs(self):
+        return [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
 
     def step_torch(self):
         import torch
@@ -213,9 +225,244 @@ class MapReduce(Workload):
         return self.bytes / dt / GB, "full workload: 2^26 elements, one oracle pass", 1
 
 
+class Stencil(Workload):
+    """Iterated stencil workloads; bytes follow the per-step convention
+    (every step reads and writes the whole grid once: 2 * T * cells * size)."""
+
+    def __init__(self, name):
+        self.name = name
+        import numpy as np
+        if name == "jacobi2d":
+            self.shape, self.T, self.bc, self.dtype = (256, 256), 10, "zero", "f64"
+        elif name == "heat3d":
+            self.shape, self.T, self.bc, self.dtype = (512, 512, 512), 50, "periodic", "f64"
+        else:
+            raise SystemExit("unknown workload %s" % name)
+        self.cells = int(np.prod(self.shape))
+        self.size = 8
+        self.bytes = 2 * self.T * self.cells * self.size
+
+    def roof(self):
+        # FP64 ALU bound: 5 (2-D) / 7 (3-D) weighted terms per cell and step,
+        # each a multiply and an add except the first (2k - 1 flops)
+        npts = 5 if self.name == "jacobi2d" else 7
+        steps_per_launch = self.T / max(1, self.n_launch)
+        return "alu", (2 * npts - 1) * self.cells * steps_per_launch, "flop"
+
+    def describe(self):
+        form = ("2-D 5-point 0.2*(c+w+e+s+n)" if self.name == "jacobi2d"
+                else "3-D 7-point 0.4*c + 0.1*(6 neighbours)")
+        return {"workload": "%s, %s, %s boundary, %d steps" % (form, "x".join(map(str, self.shape)),
+                                                           self.bc, self.T),
+                "dtype": self.dtype, "algorithmic_bytes_per_step": self.bytes,
+                "bytes_convention": "2 * steps * cells * 8 (each step reads and writes the grid)",
+                "l2": ("working set 1 MiB: L2-resident, launch-latency bound"
+                       if self.name == "jacobi2d" else "grid 1.07 GB > L2")}
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import inputs, programs
+        self.host = [inputs.cfg1() if self.name == "jacobi2d" else inputs.cfg3()]
+        self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
+        build = programs.jacobi2d if self.name == "jacobi2d" else programs.heat3d
+        self.g = build(self.shape, self.T, self.bc, self.dtype)
+        if self.name == "jacobi2d":
+            self.g.set_option(C.DCP_OPT_USE_GRAPH, 1)
+        self.g.fuse(C.DCP_FUSE_ALL)
+        self.g0 = build(self.shape, self.T, self.bc, self.dtype, fuse=0)
+        self.out = self.g.empty_outputs(dev)
+        self.out0 = self.g0.empty_outputs(dev)
+        self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
+        self.n_launch = len(self.kernels)
+        self.n_launch0 = self.g0.n_kernels
+
+    def step(self):
+        self.g.run(self.dev, self.out)
+
+    def step_opbyop(self):
+        self.g0.run(self.dev, self.out0)
+
+    def legs(self):
+        return [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
+
+    def step_torch(self):
+        """The paper's NumPy form as torch eager ops (slices into temporaries)."""
+        import torch
+        A = self.dev[0]
+        if self.name == "jacobi2d":
+            P = torch.zeros((A.shape[0] + 2, A.shape[1] + 2), dtype=A.dtype, device=A.device)
+            P[1:-1, 1:-1] = A
+            for _ in range(self.T):
+                B = 0.2 * (P[1:-1, 1:-1] + P[1:-1, :-2] + P[1:-1, 2:] + P[2:, 1:-1] + P[:-2, 1:-1])
+                P[1:-1, 1:-1] = B
+            return P
+        U = A
+        for _ in range(self.T):
+            U = 0.4 * U + 0.1 * (torch.roll(U, 1, 2) + torch.roll(U, -1, 2) + torch.roll(U, 1, 1)
+                                 + torch.roll(U, -1, 1) + torch.roll(U, 1, 0) + torch.roll(U, -1, 0))
+        return U
+
+    def setup_e2e(self, torch):
+        import numpy as np
+        t = torch.empty(self.shape, dtype=torch.float64, pin_memory=True)
+        t.copy_(torch.from_numpy(self.host[0]))
+        self.pinned = [t.numpy()]
+        self.host_out = [np.empty(self.shape, dtype=np.float64)]
+        self.h2d = self.pinned[0].nbytes
+        self.d2h = self.host_out[0].nbytes
+
+    def step_e2e(self):
+        self.g.run_host(self.pinned, self.host_out)
+
+    def cpu_sample(self):
+        import oracle
+        from oracle import programs as OP
+        if self.name == "jacobi2d":
+            prog = OP.jacobi2d(self.shape, self.T, self.bc)
+            t0 = time.perf_counter()
+            oracle.run(prog, self.host)
+            dt = time.perf_counter() - t0
+            return self.bytes / dt / GB, "full workload (256^2, 10 steps)", 1
+        # 3-D: 2 of the 50 steps on the full 512^3 grid, scaled per step
+        prog = OP.heat3d(self.shape, 2, self.bc)
+        t0 = time.perf_counter()
+        oracle.run(prog, self.host)
+        dt = time.perf_counter() - t0
+        return 2 * 2 * self.cells * 8 / dt / GB, "2 of 50 steps on the full 512^3 grid", 1
+
+
+class Batch(Workload):
+    """4096 independent 2-D 5-point instances, float32, 20 steps, one launch."""
+
+    def __init__(self, name="batch2d"):
+        self.name = name
+        self.dtype = "f32"
+        self.T = 20
+
+    def roof(self):
+        # compulsory device-memory traffic of one launch: every instance read
+        # and written once (the launch advances all instances `depth` steps)
+        return "hbm", 2 * self.cells * 4, "bytes"
+
+    def describe(self):
+        return {"workload": "4096 independent 2-D 5-point instances (0.2 weights, zero boundary), "
+                            "side log-uniform in [32, 512], 20 steps each, one batched launch",
+                "instances": len(self.sides), "cells": int(self.cells), "dtype": "f32",
+                "algorithmic_bytes_per_step": self.bytes,
+                "bytes_convention": "2 * steps * cells * 4 (each step reads and writes every grid)"}
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import inputs, programs
+        self.host = inputs.cfg4()
+        self.sides = [a.shape[0] for a in self.host]
+        self.cells = sum(a.size for a in self.host)
+        self.bytes = 2 * self.T * self.cells * 4
+        self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
+        self.g = programs.batch2d(self.sides, self.T, "zero", "f32")
+        self.g.set_option(C.DCP_OPT_USE_GRAPH, 1)
+        self.g.fuse(C.DCP_FUSE_ALL | C.DCP_BATCH)
+        self.out = self.g.empty_outputs(dev)
+        self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
+        self.n_launch = len(self.kernels)
+        # comparison forms: every instance as its own fused program, and op by op
+        self.g1 = programs.batch2d(self.sides, self.T, "zero", "f32", fuse=C.DCP_FUSE_ALL)
+        self.g0 = programs.batch2d(self.sides, self.T, "zero", "f32", fuse=0)
+        self.out1 = self.g1.empty_outputs(dev)
+        self.out0 = self.g0.empty_outputs(dev)
+
+    def step(self):
+        self.g.run(self.dev, self.out)
+
+    def legs(self):
+        return [("unbatched_fused", lambda: self.g1.run(self.dev, self.out1), self.g1.n_kernels),
+                ("op_by_op", lambda: self.g0.run(self.dev, self.out0), self.g0.n_kernels)]
+
+    def setup_e2e(self, torch):
+        self.h2d = self.d2h = None
+
+    def step_e2e(self):
+        return None
+
+    def cpu_sample(self):
+        import oracle
+        from oracle import programs as OP
+        sample = self.host[:64]
+        cells = sum(a.size for a in sample)
+        t0 = time.perf_counter()
+        for a in sample:
+            oracle.run(OP.jacobi2d(a.shape, self.T, "zero"), [a])
+        dt = time.perf_counter() - t0
+        return 2 * self.T * cells * 4 / dt / GB, "first 64 of 4096 instances, all 20 steps", 1
+
+
+class Adjoint(Workload):
+    """Reverse pass of u_{t+1} = tanh(S u_t), loss = sum(u_T^2), 256^3 f64, T = 20."""
+
+    metric = "adjoint steps/s"
+    unit = "steps/s"
+
+    def __init__(self, name="tanh_adjoint"):
+        self.name = name
+        self.dtype = "f64"
+        self.shape, self.T = (256, 256, 256), 20
+        self.bytes = None
+
+    def value(self, t_step):
+        return self.T / t_step
+
+    def roof(self):
+        # FP64 ALU bound; count the stencil arithmetic only (13 flops per cell per
+        # forward step and per reverse step), tanh and its derivative excluded
+        cells = 256 ** 3
+        return "alu", 13 * cells * 2 * self.T / max(1, self.n_launch), "flop"
+
+    def describe(self):
+        return {"workload": "reverse pass of u_{t+1} = tanh(S7 u_t), loss = sum(u_T^2); 256^3 f64, "
+                            "20 steps, periodic; forward tape + 20 reverse steps per call",
+                "dtype": "f64", "tape": "full (20 states, 2.7 GB)"}
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import inputs, programs
+        self.host = [inputs.cfg5()]
+        self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
+        self.g = programs.tanh_chain(self.shape, self.T, fuse=C.DCP_FUSE_ALL)
+        self.ones = [torch.ones((), dtype=torch.float64, device=dev)]
+        self.grad = [torch.empty_like(self.dev[0])]
+        self.kernels = []
+        self.n_launch = 2 * self.T
+        self.g0 = programs.tanh_chain(self.shape, self.T, fuse=0)
+        self.grad0 = [torch.empty_like(self.dev[0])]
+
+    def step(self):
+        self.g.adjoint(self.dev, self.ones, self.grad)
+
+    def legs(self):
+        return [("op_by_op", lambda: self.g0.adjoint(self.dev, self.ones, self.grad0), None)]
+
+    def cpu_sample(self):
+        import oracle
+        from oracle import programs as OP
+        shape = (64, 64, 64)
+        prog = OP.tanh_chain(shape, self.T)
+        u = self.host[0][:64, :64, :64].copy()
+        t0 = time.perf_counter()
+        oracle.adjoint(prog, [u], [1.0])
+        dt = time.perf_counter() - t0
+        scale = 64 ** 3 / 256 ** 3
+        return self.T / dt * scale, "64^3 sub-grid, 20 steps, scaled by cells to 256^3", 1
+
+
 def make_workload(name, n=None):
     if name in ("map_reduce_f32", "map_reduce_f64"):
         return MapReduce(name[-3:], n or (1 << 26))
+    if name in ("jacobi2d", "heat3d"):
+        return Stencil(name)
+    if name == "batch2d":
+        return Batch()
+    if name == "tanh_adjoint":
+        return Adjoint()
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -248,6 +495,26 @@ def _per_launch(torch, fn, steps, stream):
     return statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
 
 
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (DFMA counted as 2 flops)
+
+
+def _roofline(wl, per_launch_s):
+    """Roofline of the dominant kernel from its algorithmic work per launch."""
+    bound, work, unit = wl.roof()
+    if bound == "hbm":
+        peak, src = _peaks()
+        achieved = work / per_launch_s / GB
+        return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(wl.kernels[0]),
+                "kernel": wl.kernels[0], "peak_source": src}
+    achieved = work / per_launch_s / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
+            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
+            "traffic": _ncu_traffic(wl.kernels[0]) if wl.kernels else None,
+            "kernel": wl.kernels[0] if wl.kernels else None,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (probe measured 1.20)"}
+
+
 def run_dcp(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -268,69 +535,68 @@ def run_dcp(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(t):
+        if dist is None:
+            return t
+        tt = torch.tensor([t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
     for _ in range(args.warmup):
         wl.step()
     barrier()
     with ClockSampler(local) as clk:
         t = _time_device(torch, wl.step, args.steps, stream)
         barrier()
-    if dist is not None:
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * wl.bytes * args.steps / t / GB
+    t = max_over_ranks(t)
+    t_step = t / args.steps
+    value = world * wl.value(t_step)
 
-    # comparison forms and roofline (rank-local)
-    per_launch = _per_launch(torch, wl.step, max(5, args.steps), stream)
+    # the dominant kernel: average launch duration inside a step
+    per_launch = _per_launch(torch, wl.step, max(5, min(args.steps, 20)), stream) / max(1, wl.n_launch)
     if args.quick:
         if rank == 0:
-            print(json.dumps({"quick": True, "workload": wl.name, "elements": wl.n,
-                              "ms_per_step": t / args.steps * 1e3,
-                              "value": world * wl.bytes * args.steps / t / GB,
-                              "per_launch_ms": per_launch * 1e3,
+            print(json.dumps({"quick": True, "workload": wl.name, "ms_per_step": t_step * 1e3,
+                              "value": value, "per_launch_ms": per_launch * 1e3,
                               "kernels": wl.kernels}), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
-    for _ in range(2):
-        wl.step_opbyop()
-    t_op = _time_device(torch, wl.step_opbyop, max(3, args.steps // 2), stream) / max(3, args.steps // 2)
-    for _ in range(2):
-        wl.step_torch()
-    t_torch = _time_device(torch, wl.step_torch, max(3, args.steps // 2), stream) / max(3, args.steps // 2)
-
-    # end to end through the C ABI with host buffers
-    wl.setup_e2e(torch)
-    for _ in range(2):
+    extra = {}
+    for name, fn, nk in wl.legs():
+        k = max(3, min(args.steps // 2, 10))
+        fn()
+        t_leg = _time_device(torch, fn, k, stream) / k
+        extra[name] = {"value": round(wl.value(t_leg), 3), "unit": wl.unit,
+                       "kernels_per_step": nk, "speedup_fused": round(t_leg / t_step, 3)}
+    e2e = None
+    wl.setup_e2e(torch) if hasattr(wl, "setup_e2e") else None
+    if getattr(wl, "h2d", None):
         wl.step_e2e()
-    k_e2e = max(3, min(args.steps, 10))
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        wl.step_e2e()
-    torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - t0) / k_e2e
-    if dist is not None:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+        k_e2e = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            wl.step_e2e()
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+        e2e = {"value": round(world * wl.value(t_e2e), 2), "unit": wl.unit,
+               "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h}
 
     if rank != 0:
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return
-    peak, peak_kind = _peaks()
-    achieved = wl.bytes / per_launch / GB
-    kname = wl.kernels[0] if wl.kernels else None
     cpu_value, cpu_sample, cores = wl.cpu_sample()
     line = {
         "metric": wl.metric,
-        "value": round(value, 2),
+        "value": round(value, 3),
         "unit": wl.unit,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(t / args.steps * 1e3, 5),
+        "ms_per_step": round(t_step * 1e3, 5),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -338,20 +604,14 @@ def run_dcp(args):
         "data": "synthetic",
         "config": dict(wl.describe(), parallelism="replicas: one independent workload per GPU"
                        if world > 1 else "single GPU"),
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(kname),
-                     "kernel": kname, "peak_source": peak_kind},
-        "cpu_baseline": {"value": round(cpu_value, 4), "unit": "GB/s", "cores": cores,
+        "roofline": _roofline(wl, per_launch),
+        "cpu_baseline": {"value": round(cpu_value, 6), "unit": wl.unit, "cores": cores,
                          "kind": "oracle", "sample": cpu_sample},
-        "e2e": {"value": round(wl.bytes / t_e2e / GB * world, 2), "unit": "GB/s",
-                "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h},
+        "e2e": e2e,
         "gpu_launches": wl.n_launch * args.steps,
         "clocks": clk.summary(),
-        "op_by_op": {"value": round(wl.bytes / t_op / GB, 2), "unit": "GB/s",
-                     "kernels_per_step": wl.n_launch0, "speedup_fused": round(t_op / (t / args.steps), 3)},
-        "torch_eager": {"value": round(wl.bytes / t_torch / GB, 2), "unit": "GB/s",
-                        "speedup_fused": round(t_torch / (t / args.steps), 3)},
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -497,9 +497,11 @@ struct AdjointState {
   }
 };
 
-static void fuse_sub(Sub& s) {
+// Sub-programs are planned with the parent program's fusion flags, so the
+// reverse pass of an op-by-op program is op-by-op too.
+static void fuse_sub(Sub& s, uint32_t flags) {
   if (!s.g) return;
-  plan_graph(*s.g, DCP_FUSE_ALL);
+  plan_graph(*s.g, flags & (DCP_FUSE_MAPS | DCP_FUSE_SUBGRAPH | DCP_TIME_TILE));
   compile_plan(*s.g);
   s.g->fused = true;
 }
@@ -510,9 +512,9 @@ void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
   if (!st.built || st.budget != budget) {
     AdjointPlan p;
     plan_adjoint(g, budget, p);
-    fuse_sub(p.forward);
-    for (Sub& x : p.seg_fwd) fuse_sub(x);
-    for (Sub& x : p.seg_rev) fuse_sub(x);
+    fuse_sub(p.forward, g.flags);
+    for (Sub& x : p.seg_fwd) fuse_sub(x, g.flags);
+    for (Sub& x : p.seg_rev) fuse_sub(x, g.flags);
     st.plan = std::move(p);
     st.budget = budget;
     st.built = true;

@@ -24,6 +24,7 @@ struct Error {
   std::string msg;
 };
 [[noreturn]] void fail(dcp_status code, const std::string& msg);
+void set_last_error(const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 void check_cu(CUresult r, const char* what);
 

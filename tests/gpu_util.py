@@ -17,7 +17,10 @@ def red_tol_for(dtype):
 
 def to_dev(a):
     import torch
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a = np.asarray(a)
+    if not a.flags.c_contiguous:
+        a = a.copy()
+    return torch.from_numpy(a).cuda()
 
 
 def to_host(t):

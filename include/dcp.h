@@ -201,6 +201,26 @@ dcp_status dcp_set_option(dcp_graph g, int32_t key, int64_t value);
  * *needed (may be NULL) receives the full length + 1. */
 dcp_status dcp_plan_info(dcp_graph g, char* buf, size_t len, size_t* needed);
 
+/* Whole-array reduction that allocates no device memory (the paper has no
+ * counterpart; it serves callers that cannot allocate: a host application
+ * whose pool allocator owns all device memory, an out-of-memory recovery
+ * path, or a caller promised a fixed footprint).  Same result as a graph
+ * input -> dcp_add_reduce -> output, up to summation order:
+ *   in     device array of n elements of `dtype` (aligned to its size)
+ *   n      0 <= n <= 2^31 elements; larger n returns DCP_E_INVALID_ARG
+ *   red    DCP_SUM / DCP_MAX_R / DCP_MIN_R / DCP_MAXABS (not SUM: n >= 1)
+ *   out    device pointer to one element of `dtype`, overwritten
+ * Scratch is a fixed array inside the library (512 KiB + 256 B on every
+ * device that calls it, kept until the process exits); it never calls
+ * cudaMalloc or cudaFree.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call outside any
+ * CUDA stream capture.  Every call shares the one array, so calls whose
+ * work overlaps on the GPU (different streams, no ordering between them)
+ * race and give wrong results: order them on one stream.  Asynchronous on
+ * `cuda_stream`. */
+dcp_status dcp_reduce_noalloc(const void* in, int64_t n, int32_t dtype, int32_t red, void* out,
+                              void* cuda_stream);
+
 /* Thread-local message for the last failing call on this thread. */
 const char* dcp_last_error(void);
 

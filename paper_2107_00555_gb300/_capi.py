@@ -87,6 +87,8 @@ _SIG = [
     ("dcp_set_option", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64]),
     ("dcp_plan_info", ctypes.c_int32, [_P, ctypes.c_char_p, ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)]),
+    ("dcp_reduce_noalloc", ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                            _P, _P]),
     ("dcp_last_error", ctypes.c_char_p, []),
     ("dcp_version", ctypes.c_char_p, []),
 ]
@@ -205,6 +207,11 @@ def dcp_plan_info(g):
     buf = ctypes.create_string_buffer(need.value)
     _check("dcp_plan_info", load().dcp_plan_info(g, buf, need.value, None))
     return buf.value.decode()
+
+
+def dcp_reduce_noalloc(in_ptr, n, dtype, red, out_ptr, stream=0):
+    _check("dcp_reduce_noalloc", load().dcp_reduce_noalloc(in_ptr, int(n), dtype, red, out_ptr,
+                                                           stream))
 
 
 def dcp_last_error():

@@ -210,9 +210,19 @@ class MapReduce(Workload):
         self.host_out = [np.empty((), dtype=_np_dtype(self.dtype)) for _ in range(2)]
         self.h2d = sum(a.nbytes for a in self.pinned)
         self.d2h = sum(o.nbytes for o in self.host_out)
+        # the same call forced through device staging copies, for comparison
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import programs
+        self.g_staged = programs.map_reduce(self.n, self.dtype)
+        self.g_staged.set_option(C.DCP_OPT_HOST_ACCESS, 0)
+        self.g_staged.fuse(C.DCP_FUSE_ALL)
 
     def step_e2e(self):
+        # page-locked host buffers: the fused kernel reads them directly
         self.g.run_host(self.pinned, self.host_out)
+
+    def step_e2e_staged(self):
+        self.g_staged.run_host(self.pinned, self.host_out)
 
     def cpu_sample(self):
         """Oracle on the full workload (2**26 elements), single thread."""
@@ -498,6 +508,22 @@ def _per_launch(torch, fn, steps, stream):
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (DFMA counted as 2 flops)
 
 
+def reduce_max(value, dist=None, device=None):
+    """Largest `value` over all ranks.  Used for timing only: the workload
+    itself has no collective (every rank runs an independent instance)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(per_rank_work, world, t_max):
+    """Whole-job throughput: the work of all ranks over the slowest rank's time."""
+    return world * per_rank_work / t_max
+
+
 def _roofline(wl, per_launch_s):
     """Roofline of the dominant kernel from its algorithmic work per launch."""
     bound, work, unit = wl.roof()
@@ -536,11 +562,7 @@ def run_dcp(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(t):
-        if dist is None:
-            return t
-        tt = torch.tensor([t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return reduce_max(t, dist, dev)
 
     for _ in range(args.warmup):
         wl.step()
@@ -550,7 +572,7 @@ def run_dcp(args):
         barrier()
     t = max_over_ranks(t)
     t_step = t / args.steps
-    value = world * wl.value(t_step)
+    value = weak_scaling_value(wl.value(t_step) * t_step, world, t_step)
 
     # the dominant kernel: average launch duration inside a step
     per_launch = _per_launch(torch, wl.step, max(5, min(args.steps, 20)), stream) / max(1, wl.n_launch)
@@ -582,6 +604,16 @@ def run_dcp(args):
         t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
         e2e = {"value": round(world * wl.value(t_e2e), 2), "unit": wl.unit,
                "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h}
+        if hasattr(wl, "step_e2e_staged"):
+            wl.step_e2e_staged()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                wl.step_e2e_staged()
+            torch.cuda.synchronize()
+            t_st = max_over_ranks((time.perf_counter() - t0) / k_e2e)
+            extra["e2e_staged_copies"] = {"value": round(world * wl.value(t_st), 2),
+                                          "unit": wl.unit}
 
     if rank != 0:
         if dist is not None:

@@ -33,9 +33,9 @@
  *    outputs must not overlap.
  *  - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default
  *    stream).  dcp_run* enqueue work asynchronously on it and return once
- *    the work is enqueued; the caller synchronises.  Errors a kernel detects
- *    on the device (a bounded wait that expired) are latched in a device
- *    status word and reported by dcp_sync().
+ *    the work is enqueued; the caller synchronises.  No kernel waits on
+ *    another thread block, so no launch can hang on a lost peer; dcp_sync()
+ *    reports asynchronous CUDA errors of the stream.
  *  - Thread safety: one graph must not be used by two threads at once;
  *    different graphs are independent.
  */
@@ -62,7 +62,7 @@ enum {
   DCP_E_OOM = -5,         /* device or host allocation failed (or budget exceeded) */
   DCP_E_CUDA = -6,        /* a CUDA runtime/driver call failed (message has detail) */
   DCP_E_COMPILE = -7,     /* run-time compilation of a fused kernel failed */
-  DCP_E_TIMEOUT = -8,     /* a bounded device-side wait expired */
+  DCP_E_TIMEOUT = -8,     /* reserved: a bounded device-side wait expired */
   DCP_E_STATE = -9        /* call not allowed in the graph's current state */
 };
 
@@ -113,7 +113,9 @@ enum {
   DCP_OPT_TILE_Y = 3,          /* stencil tile extent along y */
   DCP_OPT_MAP_BLOCKS_PER_SM = 4, /* CTAs per SM for map/reduce kernels */
   DCP_OPT_USE_GRAPH = 5,       /* 1: replay a captured CUDA graph in dcp_run */
-  DCP_OPT_WAIT_LIMIT = 6       /* iteration limit of bounded device waits (test hook) */
+  DCP_OPT_STENCIL_KERNEL = 7,  /* 2-D stencils: 0 shared-memory tiles, 1 warp stream */
+  DCP_OPT_HOST_ACCESS = 8      /* dcp_run_host: 1 (default) kernels access page-locked host
+                                  buffers directly, 0 always stage through device copies */
 };
 
 /* ---- graph construction ------------------------------------------------ */
@@ -170,9 +172,11 @@ dcp_status dcp_fuse(dcp_graph g, uint32_t flags, int32_t* n_kernels_out);
 dcp_status dcp_run(dcp_graph g, const void* const* inputs, void* const* outputs,
                    void* cuda_stream);
 
-/* As dcp_run, but inputs and outputs are HOST pointers: copies the inputs
- * to graph-owned device staging buffers, runs, copies the outputs back and
- * waits for the stream.  Host buffers in page-locked memory copy fastest. */
+/* As dcp_run, but inputs and outputs are HOST pointers, and the call waits
+ * for the stream before returning.  When every buffer is page-locked
+ * (cudaHostAlloc / cudaHostRegister) the kernels read and write the host
+ * buffers directly; otherwise the inputs are copied to graph-owned device
+ * staging buffers and the outputs copied back (DCP_OPT_HOST_ACCESS). */
 dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const* host_outputs,
                         void* cuda_stream);
 
@@ -188,8 +192,7 @@ dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const
 dcp_status dcp_run_adjoint(dcp_graph g, const void* const* inputs, const void* const* out_grads,
                            void* const* in_grads, size_t tape_budget_bytes, void* cuda_stream);
 
-/* Waits for `cuda_stream` and reports device-side errors latched by this
- * graph's kernels (DCP_E_TIMEOUT for an expired bounded wait). */
+/* Waits for `cuda_stream` and reports asynchronous CUDA errors. */
 dcp_status dcp_sync(dcp_graph g, void* cuda_stream);
 
 /* Overrides a planner choice (DCP_OPT_*).  Allowed before dcp_fuse (tile and

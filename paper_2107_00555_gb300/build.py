@@ -30,7 +30,7 @@ EMBED = [("dcp_device.cuh", "device_header_source"),
          ("k_map.cuh", "kernel_map_source"),
          ("k_stencil2d.cuh", "kernel_stencil2d_source"),
          ("k_stencil3d.cuh", "kernel_stencil3d_source"),
-         ("k_adjoint.cuh", "kernel_adjoint_source")]
+         ("k_stencil2d_stream.cuh", "kernel_stream_source")]
 
 
 def _embed_source() -> str:

@@ -347,10 +347,11 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
       case DCP_OPT_TILE_X:
       case DCP_OPT_TILE_Y:
       case DCP_OPT_MAP_BLOCKS_PER_SM:
+      case DCP_OPT_STENCIL_KERNEL:
         if (g.fused) fail(DCP_E_STATE, "tiling options must be set before dcp_fuse");
         break;
       case DCP_OPT_USE_GRAPH:
-      case DCP_OPT_WAIT_LIMIT:
+      case DCP_OPT_HOST_ACCESS:
         break;
       default:
         fail(DCP_E_INVALID_ARG, "unknown option key " + std::to_string(key));

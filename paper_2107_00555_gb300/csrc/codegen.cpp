@@ -197,7 +197,70 @@ std::string epi_body(const GraphImpl& g, const StepDesc& s) {
 
 }  // namespace
 
+// Warp-stream form (k_stencil2d_stream.cuh) of a 1-D / 2-D stencil launch.
+static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
+  const bool batch = G.kind == GroupKind::Batch;
+  const int nd = batch ? 2 : (int)G.shape.size();
+  const int T = G.dtype;
+  const int nsteps = s1 - s0;
+  const bool first = s0 == 0, last = s1 == (int)G.steps.size();
+  const int C = stream_cols_per_lane(T);
+  const int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
+  const int NR = 2 * ry + 1;
+  const int RXA = rx > 0 ? rx : 1;
+  std::ostringstream os;
+  os << "// dcp warp-stream stencil kernel: steps [" << s0 << ", " << s1 << ") of "
+     << G.steps.size() << ", bc " << G.bc << ", " << nd << "-D" << (batch ? ", batched" : "") << "\n";
+  os << "#define DCP_T " << dtype_cname(T) << "\n#define DCP_C " << C << "\n";
+  os << "#define DCP_THREADS " << G.threads << "\n#define DCP_BC " << G.bc << "\n";
+  os << "#define DCP_LAST " << (last ? 1 : 0) << "\n#define DCP_BATCH " << (batch ? 1 : 0) << "\n";
+  os << "#define DCP_NSTORE " << (last ? (int)G.stores.size() : 1) << "\n#define DCP_NRED "
+     << (last ? (int)G.reds.size() : 0) << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n";
+  os << "#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_NSTEPS " << nsteps
+     << "\n#define DCP_SEG " << std::max(1, G.seg) << "\n";
+  os << red_op_fn(g, last ? G.reds : std::vector<int>{});
+  os << "#include \"dcp_device.cuh\"\n";
+  if (!batch) emit_stencil_io(os, g, G, first, last);
+  os << "template <int S> __device__ __forceinline__ void dcp_level(const DCP_T (&up)[" << NR << "]["
+     << C << "], const DCP_T (&lf)[" << NR << "][" << RXA << "], const DCP_T (&rt)[" << NR << "]["
+     << RXA << "], DCP_T (&out)[" << C << "]);\n";
+  os << "template <int S> __device__ __forceinline__ DCP_T dcp_epi(DCP_T v);\n";
+  for (int s = 0; s < nsteps; ++s) {
+    const StepDesc& sd = G.steps[s0 + s];
+    const Node& sn = g.nodes[sd.node];
+    os << "template <> __device__ __forceinline__ void dcp_level<" << s << ">(const DCP_T (&up)[" << NR
+       << "][" << C << "], const DCP_T (&lf)[" << NR << "][" << RXA << "], const DCP_T (&rt)[" << NR
+       << "][" << RXA << "], DCP_T (&out)[" << C << "]) {\n";
+    os << "  (void)lf; (void)rt;\n";
+    for (int c = 0; c < C; ++c) {
+      for (int k = 0; k < sn.npts(); ++k) {
+        int dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+        int cc = c + dx, row = ry + dy;
+        std::string x;
+        if (cc < 0) x = "lf[" + std::to_string(row) + "][" + std::to_string(rx + cc) + "]";
+        else if (cc >= C) x = "rt[" + std::to_string(row) + "][" + std::to_string(cc - C) + "]";
+        else x = "up[" + std::to_string(row) + "][" + std::to_string(cc) + "]";
+        std::string w = weight_literal(T, sn.weights[k]);
+        if (k == 0) os << "  DCP_T a" << c << " = dcp_mul_rn(" << w << ", " << x << ");\n";
+        else os << "  a" << c << " = dcp_fma_rn(" << w << ", " << x << ", a" << c << ");\n";
+      }
+      os << "  out[" << c << "] = a" << c << ";\n";
+    }
+    os << "}\n";
+    os << "template <> __device__ __forceinline__ DCP_T dcp_epi<" << s << ">(DCP_T v) {\n"
+       << epi_body(g, sd) << "}\n";
+  }
+  os << "#include \"k_stencil2d_stream.cuh\"\n";
+  CodegenOut out;
+  out.threads = G.threads;
+  out.smem_bytes = 0;
+  out.source = finish(batch ? "dcp_bstream" : "dcp_stream", os.str());
+  out.name = kname_of(out.source);
+  return out;
+}
+
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
+  if (G.variant == 1) return gen_stream_kernel(g, G, s0, s1);
   const bool batch = G.kind == GroupKind::Batch;
   const int nd = batch ? 2 : (int)G.shape.size();
   const int T = G.dtype;
@@ -235,9 +298,10 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
       for (int k = 0; k < sn.npts(); ++k) {
         int dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
         int off = dy * PW + dx;
-        std::string term = weight_literal(T, sn.weights[k]) + " * A[c + (" + std::to_string(off) + ")]";
-        if (k == 0) os << "  DCP_T acc = " << term << ";\n";
-        else os << "  acc = acc + " << term << ";\n";
+        std::string w = weight_literal(T, sn.weights[k]);
+        std::string x = "A[c + (" + std::to_string(off) + ")]";
+        if (k == 0) os << "  DCP_T acc = dcp_mul_rn(" << w << ", " << x << ");\n";
+        else os << "  acc = dcp_fma_rn(" << w << ", " << x << ", acc);\n";
       }
       os << "  return acc;\n}\n";
       os << "template <> __device__ __forceinline__ DCP_T dcp_epi<" << s << ">(DCP_T v) {\n"
@@ -258,10 +322,10 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     os << "__device__ __forceinline__ DCP_T dcp_sum3(const DCP_T* const* pl, int c) {\n";
     for (int k = 0; k < sn.npts(); ++k) {
       int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
-      std::string term = weight_literal(T, sn.weights[k]) + " * pl[" + std::to_string(dz + rz) +
-                         "][c + (" + std::to_string(dy * PW + dx) + ")]";
-      if (k == 0) os << "  DCP_T acc = " << term << ";\n";
-      else os << "  acc = acc + " << term << ";\n";
+      std::string w = weight_literal(T, sn.weights[k]);
+      std::string x = "pl[" + std::to_string(dz + rz) + "][c + (" + std::to_string(dy * PW + dx) + ")]";
+      if (k == 0) os << "  DCP_T acc = dcp_mul_rn(" << w << ", " << x << ");\n";
+      else os << "  acc = dcp_fma_rn(" << w << ", " << x << ", acc);\n";
     }
     os << "  return acc;\n}\n";
     os << "__device__ __forceinline__ DCP_T dcp_epi3(DCP_T v) {\n" << epi_body(g, sd) << "}\n";

@@ -126,6 +126,8 @@ struct Group {
   int tile[3] = {1, 1, 1};      // output tile (z, y, x) for stencils
   int threads = 256;
   int blocks_per_sm = 4;
+  int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
+  int seg = 0;                  // warp stream: rows per work item (single arrays)
   // batch groups: the member stencil groups (same program, different shapes)
   std::vector<int> batch_members;  // indices into Plan::groups of absorbed groups
   bool absorbed = false;           // this stencil group runs inside a batch group
@@ -158,7 +160,7 @@ const char* device_header_source();     // dcp_device.cuh
 const char* kernel_map_source();        // k_map.cuh
 const char* kernel_stencil2d_source();  // k_stencil2d.cuh
 const char* kernel_stencil3d_source();  // k_stencil3d.cuh
-const char* kernel_adjoint_source();    // k_adjoint.cuh
+const char* kernel_stream_source();     // k_stencil2d_stream.cuh
 
 // ---------------------------------------------------------------------------
 // Graph object
@@ -220,6 +222,13 @@ CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int 
 uint64_t fnv1a(const std::string& s);
 
 constexpr int kMaxIO = 16;       // loads / stores / reductions per kernel
+
+// Warp-stream stencil geometry: columns per lane and columns written per warp.
+inline int stream_cols_per_lane(int dtype) { return dtype == DCP_F64 || dtype == DCP_I64 ? 2 : 4; }
+inline int stream_width(const Group& G) {
+  return 32 * stream_cols_per_lane(G.dtype) - 2 * G.depth * G.radius[2];
+}
+bool stream_eligible(const Group& G, int depth);
 constexpr int kMaxRadius = 4;
 constexpr int kMaxPoints = 32;
 

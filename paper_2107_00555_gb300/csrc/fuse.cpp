@@ -397,6 +397,30 @@ struct Planner {
   }
 
   void choose_stencil_tiling(Group& G) {
+    choose_stencil_tiling_impl(G);
+    // the warp-stream kernel when it applies (zero / fixed-ring boundary, 1-D
+    // or 2-D, radius <= 2); the shared-memory tile kernel otherwise
+    int var = stream_eligible(G, G.depth) ? 1 : 0;
+    auto it = g.options.find(DCP_OPT_STENCIL_KERNEL);
+    if (it != g.options.end()) var = (it->second == 1 && stream_eligible(G, G.depth)) ? 1 : 0;
+    G.variant = var;
+    if (var == 1) {
+      G.threads = 128;
+      if (G.kind != GroupKind::Batch) {
+        // rows per work item: enough items to fill the GPU, and at least
+        // 8 * depth * radius rows so warm-up rows stay a small fraction
+        int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1;
+        int64_t nx = G.shape.back();
+        int64_t strips = (nx + stream_width(G) - 1) / stream_width(G);
+        int64_t target_items = 152 * 16;
+        int64_t seg = (ny * strips + target_items - 1) / target_items;
+        seg = std::max<int64_t>(seg, 8 * G.depth * std::max(1, G.radius[1]));
+        G.seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), std::max<int64_t>(ny, 1));
+      }
+    }
+  }
+
+  void choose_stencil_tiling_impl(Group& G) {
     int S = (int)G.steps.size();
     bool tt = flags & DCP_TIME_TILE;
     int nd = G.kind == GroupKind::Batch ? 2 : (int)G.shape.size();
@@ -422,6 +446,15 @@ struct Planner {
 };
 
 }  // namespace
+
+bool stream_eligible(const Group& G, int depth) {
+  const int nd = G.kind == GroupKind::Batch ? 2 : (int)G.shape.size();
+  if (nd > 2 || G.bc == DCP_BC_PERIODIC) return false;
+  if (G.radius[1] > 2 || G.radius[2] > 2) return false;
+  const int C = stream_cols_per_lane(G.dtype);
+  if (G.radius[2] > C) return false;
+  return 32 * C - 2 * depth * G.radius[2] >= 8;
+}
 
 void plan_graph(GraphImpl& g, uint32_t flags) {
   g.flags = flags;

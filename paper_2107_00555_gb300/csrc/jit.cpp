@@ -68,18 +68,26 @@ std::vector<char> nvrtc_compile(const std::string& src, const std::string& name,
   }
   auto t0 = std::chrono::steady_clock::now();
   const char* hdr_src[] = {device_header_source(), kernel_map_source(), kernel_stencil2d_source(),
-                           kernel_stencil3d_source()};
-  const char* hdr_name[] = {"dcp_device.cuh", "k_map.cuh", "k_stencil2d.cuh", "k_stencil3d.cuh"};
+                           kernel_stencil3d_source(), kernel_stream_source()};
+  const char* hdr_name[] = {"dcp_device.cuh", "k_map.cuh", "k_stencil2d.cuh", "k_stencil3d.cuh",
+                            "k_stencil2d_stream.cuh"};
   nvrtcProgram prog;
-  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 4, hdr_src,
+  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 5, hdr_src,
                                      hdr_name);
   if (r != NVRTC_SUCCESS) fail(DCP_E_COMPILE, std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r));
-  r = nvrtcCompileProgram(prog, (int)(sizeof kOpts / sizeof kOpts[0]), kOpts);
+  // DCP_PTXAS_VERBOSE=1 prints the assembler's register / spill report of
+  // every compiled kernel to stderr (a diagnostic; needs no GPU)
+  const char* verbose = std::getenv("DCP_PTXAS_VERBOSE");
+  const bool vb = verbose && *verbose == '1';
+  std::vector<const char*> opts(kOpts, kOpts + sizeof kOpts / sizeof kOpts[0]);
+  if (vb) opts.push_back("--ptxas-options=-v");
+  r = nvrtcCompileProgram(prog, (int)opts.size(), opts.data());
   size_t logsz = 0;
   nvrtcGetProgramLogSize(prog, &logsz);
   std::string log(logsz, '\0');
   if (logsz) nvrtcGetProgramLog(prog, &log[0]);
   if (log_out) *log_out = log;
+  if (vb && r == NVRTC_SUCCESS) std::fprintf(stderr, "[dcp] %s:\n%s\n", name.c_str(), log.c_str());
   if (r != NVRTC_SUCCESS) {
     nvrtcDestroyProgram(&prog);
     fail(DCP_E_COMPILE, "NVRTC failed for " + name + ": " + log);

@@ -62,6 +62,14 @@ __device__ __forceinline__ float dcp_div(float a, float b) { return a / b; }
 __device__ __forceinline__ double dcp_div(double a, double b) { return a / b; }
 
 template <typename T> __device__ __forceinline__ T dcp_square(T a) { return dcp_mul(a, a); }
+
+// Stencil weighted sums use explicit rounding intrinsics so that every kernel
+// form (tile, stream, batched, any time-tile depth) performs bit-identical
+// per-step arithmetic: acc = w0*x0, then acc = fma(wk, xk, acc) in point order.
+__device__ __forceinline__ float dcp_mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double dcp_mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float dcp_fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double dcp_fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <typename T> __device__ __forceinline__ T dcp_sign(T a) {
   return a > (T)0 ? (T)1 : (a < (T)0 ? (T)-1 : (T)0);
 }

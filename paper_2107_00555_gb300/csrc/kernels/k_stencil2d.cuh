@@ -42,11 +42,41 @@ __device__ __forceinline__ int dcp_wrap(int q, int n) {
   return r < 0 ? r + n : r;
 }
 
+// One step over the region that is still valid after S+1 steps.  Tiles
+// whose region lies where the step needs no boundary treatment (inside the
+// array, outside the fixed ring; always under PERIODIC, whose halo holds
+// wrapped copies) take the fast path: each work item is R consecutive rows of
+// one column, all loads are issued before any store, so the R weighted sums
+// share the shared-memory loads of their common neighbours.  Other tiles take
+// the checked path, one cell per work item.
 template <int S>
 __device__ __forceinline__ void dcp_run_step(const T* __restrict__ A, T* __restrict__ B, int y0,
                                              int x0, int ny, int nx) {
   constexpr int my = (S + 1) * DCP_RY, mx = (S + 1) * DCP_RX;
   constexpr int RH = DCP_PH - 2 * my, RW = DCP_PW - 2 * mx;
+  constexpr int R = (RH % 4 == 0) ? 4 : ((RH % 2 == 0) ? 2 : 1);
+  constexpr int NB = RH / R;
+  const int ry0 = y0 + my, rx0 = x0 + mx;  // global coordinates of the region's corner
+  bool fast;
+  if (DCP_BC == DCP_BC_PERIODIC) {
+    fast = true;
+  } else {
+    const int lo_y = DCP_BC == DCP_BC_FIXED_RING ? DCP_RY : 0;
+    const int lo_x = DCP_BC == DCP_BC_FIXED_RING ? DCP_RX : 0;
+    fast = ry0 >= lo_y && ry0 + RH <= ny - lo_y && rx0 >= lo_x && rx0 + RW <= nx - lo_x;
+  }
+  if (fast) {
+    for (int i = threadIdx.x; i < NB * RW; i += DCP_THREADS) {
+      const int rb = i / RW, lx = mx + (i - rb * RW);
+      const int c0 = (my + rb * R) * DCP_PW + lx;
+      T v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = dcp_sum<S>(A, c0 + r * DCP_PW);
+#pragma unroll
+      for (int r = 0; r < R; ++r) B[c0 + r * DCP_PW] = dcp_epi<S>(v[r]);
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < RH * RW; i += DCP_THREADS) {
     const int ly = my + i / RW, lx = mx + i % RW;
     const int c = ly * DCP_PW + lx;

@@ -1,0 +1,286 @@
+// k_stencil2d_stream.cuh -- register-resident, warp-streamed time tiling of
+// a 1-D / 2-D iterated stencil (zero or fixed-ring boundary).
+//
+// A warp owns a strip of 32*C consecutive columns (C per lane) and streams
+// down the rows of its strip.  The DCP_NSTEPS steps of one launch are kept as
+// a pipeline of time levels in registers: when input row j arrives (level 0),
+// level l computes row j - l*RY from the 2*RY+1 most recent rows of level
+// l-1, so each row passes through all levels while it is in registers.
+// Neighbours along x come from the adjacent lanes by warp shuffles; the strip
+// loses RX columns of validity per level at each edge, so a warp writes
+// W = 32*C - 2*NSTEPS*RX columns.  There is no shared memory and no barrier
+// inside the stream; device memory is read once (plus the strip overlap) and
+// written once per NSTEPS steps.
+//
+// Work items are (array, strip, row segment); a segment streams its rows plus
+// NSTEPS*RY warm-up rows above it.  Warps stride through the items (items of
+// the largest arrays first in batched launches).
+//
+// The generated prefix defines DCP_T, DCP_C, DCP_RX, DCP_RY, DCP_NSTEPS,
+// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_SEG,
+// DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
+//   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
+//   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
+//                     T (&out)[C])   weighted sum of step L (rows up[RY+dy]),
+//   T    dcp_epi<L>(T v)                 epilogue maps fused after step L
+//   void dcp_post(const DcpStParams& p, const T* sc, long long i, T v, T* st, T* rv)
+typedef DCP_T T;
+typedef typename DcpFin<T>::type F;
+#define DCP_ARR(n) ((n) > 0 ? (n) : 1)
+
+#define DCP_BC_ZERO 0
+#define DCP_BC_PERIODIC 1
+#define DCP_BC_FIXED_RING 2
+
+constexpr int NR = 2 * DCP_RY + 1;                 // rows kept per level
+constexpr int K = DCP_NSTEPS;
+constexpr int C = DCP_C;
+constexpr int SPAN = 32 * C;                       // columns held by a warp
+constexpr int W = SPAN - 2 * K * DCP_RX;           // columns written by a warp
+static_assert(W > 0, "strip too narrow for the number of steps");
+constexpr int RXA = DCP_RX > 0 ? DCP_RX : 1;
+
+typedef DcpStParamsT<T> DcpStParams;
+
+__device__ __forceinline__ constexpr int dcp_mod(int a, int m) { return ((a % m) + m) % m; }
+
+// One array (or instance) and the part of it a work item covers.
+struct DcpItem {
+  const T* in;   // batched: instance input; single: unused (dcp_input reads p.ld)
+  T* out;        // batched: instance output
+  int ny, nx;
+  int x0;        // first written column
+  int y0, y1;    // rows written
+};
+
+template <int L, int P>
+__device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], int j,
+                                               const DcpItem& it, int col0, T (&outv)[C],
+                                               bool& out_ok) {
+  // level L (1-based) computes row y = j - L*RY from level L-1
+  constexpr int l = L - 1;  // source level
+  const int y = j - L * DCP_RY;
+  T up[NR][C];
+#pragma unroll
+  for (int d = 0; d < NR; ++d)
+#pragma unroll
+    for (int c = 0; c < C; ++c) up[d][c] = ring[l][dcp_mod(P - L * DCP_RY + d - DCP_RY, NR)][c];
+  T lf[NR][RXA], rt[NR][RXA];
+#pragma unroll
+  for (int d = 0; d < NR; ++d)
+#pragma unroll
+    for (int q = 0; q < DCP_RX; ++q) {
+      lf[d][DCP_RX - 1 - q] = __shfl_up_sync(0xffffffffu, up[d][C - 1 - q], 1);
+      rt[d][q] = __shfl_down_sync(0xffffffffu, up[d][q], 1);
+    }
+  T v[C];
+  dcp_level<L - 1>(up, lf, rt, v);
+  const bool row_in = (unsigned)y < (unsigned)it.ny;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int col = col0 + c;
+    const bool in = row_in && (unsigned)col < (unsigned)it.nx;
+    T r;
+    if (!in) {
+      r = (T)0;
+    } else if (DCP_BC == DCP_BC_FIXED_RING &&
+               (y < DCP_RY || y >= it.ny - DCP_RY || col < DCP_RX || col >= it.nx - DCP_RX)) {
+      r = dcp_epi<L - 1>(up[DCP_RY][c]);  // ring cell keeps its value; epilogue still applies
+    } else {
+      r = dcp_epi<L - 1>(v[c]);
+    }
+    v[c] = r;
+  }
+  if constexpr (L < K) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) ring[L][dcp_mod(P - L * DCP_RY, NR)][c] = v[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) outv[c] = v[c];
+    out_ok = row_in;
+  }
+}
+
+template <int L, int P>
+__device__ __forceinline__ void dcp_levels(T (&ring)[K > 1 ? K : 1][NR][C], int j,
+                                           const DcpItem& it, int col0, T (&outv)[C],
+                                           bool& out_ok) {
+  if constexpr (L <= K) {
+    dcp_level_step<L, P>(ring, j, it, col0, outv, out_ok);
+    dcp_levels<L + 1, P>(ring, j, it, col0, outv, out_ok);
+  }
+}
+
+constexpr int PD = 4;  // input rows in flight (software prefetch distance)
+
+template <class Input>
+__device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem& it, int col0,
+                                              Input& input) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int col = col0 + c;
+    dst[c] = ((unsigned)j < (unsigned)it.ny && (unsigned)col < (unsigned)it.nx)
+                 ? input((long long)j * it.nx + col)
+                 : (T)0;
+  }
+}
+
+// One stream iteration: input row j (phase P = j mod NR).  Row j comes from
+// the head of the prefetch queue; row j + PD is requested before the levels
+// are computed, so its load latency overlaps PD iterations of arithmetic.
+template <int P, class Input, class Output>
+__device__ __forceinline__ void dcp_iter(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
+                                         const DcpItem& it, int col0, Input& input,
+                                         Output& output) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) ring[0][P][c] = q[0][c];
+#pragma unroll
+  for (int k = 0; k + 1 < PD; ++k)
+#pragma unroll
+    for (int c = 0; c < C; ++c) q[k][c] = q[k + 1][c];
+  dcp_fetch_row(q[PD - 1], j + PD, it, col0, input);
+  T outv[C];
+  bool out_ok = false;
+  dcp_levels<1, P>(ring, j, it, col0, outv, out_ok);
+  const int y = j - K * DCP_RY;
+  if (out_ok && y >= it.y0 && y < it.y1) output(y, outv);
+}
+
+template <class Input, class Output>
+__device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Output&& output) {
+  const int lane = threadIdx.x & 31;
+  const int col0 = it.x0 - K * DCP_RX + lane * C;
+  T ring[K > 1 ? K : 1][NR][C];
+#pragma unroll
+  for (int l = 0; l < (K > 1 ? K : 1); ++l)
+#pragma unroll
+    for (int d = 0; d < NR; ++d)
+#pragma unroll
+      for (int c = 0; c < C; ++c) ring[l][d][c] = (T)0;
+  int j = it.y0 - K * DCP_RY;
+  const int jend = it.y1 + K * DCP_RY;
+  T q[PD][C];
+#pragma unroll
+  for (int k = 0; k < PD; ++k) dcp_fetch_row(q[k], j + k, it, col0, input);
+  // Rows before the first streamed row hold zeros: exact ghosts above the
+  // array; inside the array they only feed warm-up rows that are never
+  // written.  Iterations run in groups of NR so that every ring index is a
+  // compile-time constant (phase = j mod NR); first align j to a group start.
+  while (j < jend && dcp_mod(j, NR) != 0) {
+    switch (dcp_mod(j, NR)) {
+      case 1: dcp_iter<1 % NR>(ring, q, j, it, col0, input, output); break;
+      case 2: dcp_iter<2 % NR>(ring, q, j, it, col0, input, output); break;
+      case 3: dcp_iter<3 % NR>(ring, q, j, it, col0, input, output); break;
+      case 4: dcp_iter<4 % NR>(ring, q, j, it, col0, input, output); break;
+      default: break;
+    }
+    ++j;
+  }
+  for (; j + NR <= jend; j += NR) {
+    dcp_iter<0>(ring, q, j, it, col0, input, output);
+    if constexpr (NR > 1) dcp_iter<1 % NR>(ring, q, j + 1, it, col0, input, output);
+    if constexpr (NR > 2) dcp_iter<2 % NR>(ring, q, j + 2, it, col0, input, output);
+    if constexpr (NR > 3) dcp_iter<3 % NR>(ring, q, j + 3, it, col0, input, output);
+    if constexpr (NR > 4) dcp_iter<4 % NR>(ring, q, j + 4, it, col0, input, output);
+  }
+  for (int r = 0; j < jend; ++j, ++r) {
+    switch (r) {
+      case 0: dcp_iter<0>(ring, q, j, it, col0, input, output); break;
+      case 1: dcp_iter<1 % NR>(ring, q, j, it, col0, input, output); break;
+      case 2: dcp_iter<2 % NR>(ring, q, j, it, col0, input, output); break;
+      case 3: dcp_iter<3 % NR>(ring, q, j, it, col0, input, output); break;
+      default: break;
+    }
+  }
+}
+
+#if !DCP_BATCH
+// Single array: items = strips x row segments of DCP_SEG rows.
+extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStParams p) {
+  T sc[DCP_ARR(DCP_NSCALAR)];
+#pragma unroll
+  for (int i = 0; i < DCP_NSCALAR; ++i) sc[i] = p.sc[i][0];
+  T acc[DCP_ARR(DCP_NRED)];
+#pragma unroll
+  for (int r = 0; r < DCP_NRED; ++r) acc[r] = dcp_red_init<T>(dcp_red_op(r));
+  const int ny = p.ny, nx = p.nx;
+  const int strips = (nx + W - 1) / W;
+  const int segs = (ny + DCP_SEG - 1) / DCP_SEG;
+  const int items = strips * segs;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
+  for (int w = warp; w < items; w += nwarps) {
+    const int sg = w / strips, st = w - sg * strips;
+    DcpItem it{nullptr, nullptr, ny, nx, st * W, sg * DCP_SEG, min(ny, (sg + 1) * DCP_SEG)};
+    const int col0 = it.x0 - K * DCP_RX + lane * C;
+    dcp_stream(
+        it, [&](long long gi) { return dcp_input(p, sc, gi); },
+        [&](int y, const T (&v)[C]) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int col = col0 + c;
+            if (col < it.x0 || col >= it.x0 + W || col >= nx) continue;
+            const long long gi = (long long)y * nx + col;
+#if DCP_LAST
+            T stv[DCP_ARR(DCP_NSTORE)], rv[DCP_ARR(DCP_NRED)];
+            dcp_post(p, sc, gi, v[c], stv, rv);
+#pragma unroll
+            for (int s = 0; s < DCP_NSTORE; ++s) p.st[s][gi] = stv[s];
+#pragma unroll
+            for (int r = 0; r < DCP_NRED; ++r)
+              acc[r] = dcp_red_comb(dcp_red_op(r), acc[r], dcp_red_lift(dcp_red_op(r), rv[r]));
+#else
+            p.st[0][gi] = v[c];
+#endif
+          }
+        });
+  }
+#if DCP_LAST && DCP_NRED > 0
+  dcp_reduce_epilogue<T, DCP_NRED, DCP_THREADS>(acc, p.red_out, p.partials, p.ticket);
+#endif
+}
+#else
+// Batched form: items are (instance, strip); instances are ordered largest
+// first by the host; the item of warp w is found by binary search.
+struct DcpInst {
+  const T* in;
+  T* out;
+  int ny, nx, tiles_x, tile0;  // tiles_x = strips of the instance, tile0 = first item
+};
+struct DcpBatchParams {
+  const DcpInst* inst;
+  int ninst;
+  int total_tiles;
+};
+
+extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
+  for (int w = warp; w < p.total_tiles; w += nwarps) {
+    int lo = 0, hi = p.ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.inst[mid].tile0 <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    const DcpInst I = p.inst[lo];
+    const int st = w - I.tile0;
+    DcpItem it{I.in, I.out, I.ny, I.nx, st * W, 0, I.ny};
+    const T* in = I.in;
+    T* out = I.out;
+    const int col0 = it.x0 - K * DCP_RX + lane * C;
+    dcp_stream(
+        it, [&](long long gi) { return in[gi]; },
+        [&](int y, const T (&v)[C]) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int col = col0 + c;
+            if (col < it.x0 || col >= it.x0 + W || col >= it.nx) continue;
+            out[(long long)y * it.nx + col] = v[c];
+          }
+        });
+  }
+}
+#endif

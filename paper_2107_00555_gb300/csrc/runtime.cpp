@@ -1,11 +1,18 @@
 // Execution of a fused plan: one launch per fused group (or per time-tile
 // chunk of a stencil group), transients allocated once and reused (Sec. 3.1
 // transient allocation mitigation: temporaries are persistent, allocated when
-// the program is first run), per-group scratch for the tiled reductions, and
-// optional replay of the whole run as one captured CUDA graph.
+// the program is first run), per-group scratch for the tiled reductions,
+// optional replay of the whole run as one captured CUDA graph, and the
+// autotuner that times candidate tile shapes / time-tile depths of every
+// stencil group on the first run.
 #include <algorithm>
+#include <array>
 #include <cinttypes>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <mutex>
 #include <numeric>
 #include <sstream>
 
@@ -60,6 +67,23 @@ struct LaunchSpec {
   int occ_scalar = 1;
 };
 
+// Batch instance table of one launch (chunk) of a batch group.
+struct Table {
+  InstH* host = nullptr;  // pinned
+  void* dev = nullptr;
+  int tiles = 0;
+  std::vector<const void*> key;
+};
+
+struct GroupRT {
+  void* state[2] = {nullptr, nullptr};  // time-tile ping-pong (stencil) / slabs (batch)
+  void* partials = nullptr;
+  int partial_slots = 0;
+  unsigned* ticket = nullptr;
+  std::vector<int64_t> offsets;  // batch: element offset of each member in a slab
+  std::map<int, Table> tables;   // batch: per chunk
+};
+
 int64_t numel(const std::vector<int64_t>& s) {
   int64_t n = 1;
   for (auto v : s) n *= v;
@@ -76,27 +100,22 @@ void dims3(const std::vector<int64_t>& s, int32_t& nz, int32_t& ny, int32_t& nx)
   nx = (int32_t)d[2];
 }
 
+int group_nd(const Group& G) { return G.kind == GroupKind::Batch ? 2 : (int)G.shape.size(); }
+
 }  // namespace
 
 struct GraphImpl::Runtime {
-  std::vector<LaunchSpec> launches;
+  std::vector<LaunchSpec> launches;  // grouped by group, in execution order
   bool device_ready = false;
+  bool tuned = false;
   int device = -1;
   int sms = 0;
   std::vector<void*> allocs;
-  std::vector<void*> transient;          // per value id
-  std::vector<void*> state[2];           // per group: time-tile ping-pong
-  std::vector<void*> partials;           // per group
-  std::vector<unsigned*> tickets;        // per group
-  std::vector<int> partial_slots;        // per group: blocks that may write partials
-  // batch tables, per launch
-  std::vector<InstH*> host_tables;       // pinned
-  std::vector<void*> dev_tables;
-  std::vector<int> table_tiles;
-  std::vector<std::vector<const void*>> table_key;
+  std::vector<InstH*> pinned;
+  std::vector<void*> transient;  // per value id
+  std::vector<GroupRT> grt;      // per group
   cudaEvent_t table_ev = nullptr;
-  std::vector<int64_t> batch_offset;     // per batch member: element offset in batch state
-  void* batch_state[2] = {nullptr, nullptr};
+  bool table_ev_used = false;
   // host-buffer runs
   std::vector<void*> stage_in, stage_out;
   // graph replay
@@ -110,7 +129,7 @@ struct GraphImpl::Runtime {
       cudaDeviceSynchronize();
       if (gexec) cudaGraphExecDestroy(gexec);
       for (void* p : allocs) cudaFree(p);
-      for (InstH* h : host_tables) cudaFreeHost(h);
+      for (InstH* h : pinned) cudaFreeHost(h);
       if (table_ev) cudaEventDestroy(table_ev);
       if (cur != device && cur >= 0) cudaSetDevice(cur);
     }
@@ -123,39 +142,41 @@ GraphImpl::~GraphImpl() = default;
 // ---------------------------------------------------------------------------
 // compile: generate + NVRTC every launch of the plan (no GPU needed)
 // ---------------------------------------------------------------------------
+static std::vector<LaunchSpec> build_group_launches(GraphImpl& g, int gi) {
+  std::vector<LaunchSpec> L;
+  const Group& G = g.groups[gi];
+  if (G.kind == GroupKind::Map) {
+    LaunchSpec ls;
+    ls.group = gi;
+    ls.code = gen_map_kernel(g, G, true);
+    ls.code_scalar = gen_map_kernel(g, G, false);
+    nvrtc_compile(ls.code.source, ls.code.name, &ls.compile_ms, nullptr);
+    L.push_back(std::move(ls));
+    return L;
+  }
+  const int S = (int)G.steps.size();
+  for (int s0 = 0; s0 < S; s0 += G.depth) {
+    LaunchSpec ls;
+    ls.group = gi;
+    ls.s0 = s0;
+    ls.s1 = std::min(S, s0 + G.depth);
+    ls.code = gen_stencil_kernel(g, G, ls.s0, ls.s1);
+    if (ls.code.smem_bytes > 227 * 1024)
+      fail(DCP_E_UNSUPPORTED, "stencil tile needs " + std::to_string(ls.code.smem_bytes) +
+                                  " bytes of shared memory; lower the tile or depth");
+    nvrtc_compile(ls.code.source, ls.code.name, &ls.compile_ms, nullptr);
+    L.push_back(std::move(ls));
+  }
+  return L;
+}
+
 void compile_plan(GraphImpl& g) {
   g.rt.reset(new GraphImpl::Runtime());
-  auto& L = g.rt->launches;
   for (int gi = 0; gi < (int)g.groups.size(); ++gi) {
-    const Group& G = g.groups[gi];
-    if (G.kind == GroupKind::Map) {
-      LaunchSpec ls;
-      ls.group = gi;
-      ls.code = gen_map_kernel(g, G, true);
-      ls.code_scalar = gen_map_kernel(g, G, false);
-      double ms = 0;
-      nvrtc_compile(ls.code.source, ls.code.name, &ms, nullptr);
-      ls.compile_ms = ms;
-      L.push_back(std::move(ls));
-    } else {
-      int S = (int)G.steps.size();
-      for (int s0 = 0; s0 < S; s0 += G.depth) {
-        LaunchSpec ls;
-        ls.group = gi;
-        ls.s0 = s0;
-        ls.s1 = std::min(S, s0 + G.depth);
-        ls.code = gen_stencil_kernel(g, G, ls.s0, ls.s1);
-        if (ls.code.smem_bytes > 227 * 1024)
-          fail(DCP_E_UNSUPPORTED, "stencil tile needs " + std::to_string(ls.code.smem_bytes) +
-                                      " bytes of shared memory; lower the tile or depth");
-        double ms = 0;
-        nvrtc_compile(ls.code.source, ls.code.name, &ms, nullptr);
-        ls.compile_ms = ms;
-        L.push_back(std::move(ls));
-      }
-    }
+    std::vector<LaunchSpec> L = build_group_launches(g, gi);
+    for (auto& ls : L) g.rt->launches.push_back(std::move(ls));
   }
-  g.n_launches = (int)L.size();
+  g.n_launches = (int)g.rt->launches.size();
 }
 
 // ---------------------------------------------------------------------------
@@ -167,6 +188,18 @@ static void* dalloc(GraphImpl::Runtime& rt, size_t bytes) {
   check_cuda(cudaMalloc(&p, bytes), "cudaMalloc");
   rt.allocs.push_back(p);
   return p;
+}
+
+static void load_launch(LaunchSpec& ls) {
+  ls.fn = load_function(ls.code.source, ls.code.name, nullptr, &ls.regs);
+  if (ls.code.smem_bytes > 48 * 1024)
+    check_cu(drv().funcSetAttribute(ls.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                    ls.code.smem_bytes),
+             "cuFuncSetAttribute(max dynamic smem)");
+  int occ = 0;
+  check_cu(drv().occupancy(&occ, ls.fn, ls.code.threads, ls.code.smem_bytes), "occupancy query");
+  if (occ < 1) fail(DCP_E_UNSUPPORTED, "kernel " + ls.code.name + " cannot be resident on an SM");
+  ls.occupancy = occ;
 }
 
 static void ensure_device(GraphImpl& g) {
@@ -188,71 +221,27 @@ static void ensure_device(GraphImpl& g) {
   for (int v : g.inputs) is_io[v] = 1;
   for (int v : g.outputs) is_io[v] = 1;
   try {
-    for (auto& ls : rt.launches) {
-      ls.fn = load_function(ls.code.source, ls.code.name, nullptr, &ls.regs);
-      if (ls.code.smem_bytes > 48 * 1024)
-        check_cu(drv().funcSetAttribute(ls.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
-                                    ls.code.smem_bytes),
-                 "cuFuncSetAttribute(max dynamic smem)");
-      int occ = 0;
-      check_cu(drv().occupancy(&occ, ls.fn, ls.code.threads,
-                                                           ls.code.smem_bytes),
-               "occupancy query");
-      if (occ < 1) fail(DCP_E_UNSUPPORTED, "kernel " + ls.code.name + " cannot be resident on an SM");
-      ls.occupancy = occ;
-    }
+    for (auto& ls : rt.launches) load_launch(ls);
     for (int v = 0; v < N; ++v)
       if (g.materialized[v] && !is_io[v])
         rt.transient[v] = dalloc(rt, (size_t)g.nodes[v].numel() * dtype_size(g.nodes[v].dtype));
     const int NG = (int)g.groups.size();
-    rt.state[0].assign(NG, nullptr);
-    rt.state[1].assign(NG, nullptr);
-    rt.partials.assign(NG, nullptr);
-    rt.tickets.assign(NG, nullptr);
-    rt.partial_slots.assign(NG, 0);
+    rt.grt.assign(NG, GroupRT());
     for (int gi = 0; gi < NG; ++gi) {
       const Group& G = g.groups[gi];
-      int nch = G.kind == GroupKind::Map ? 1 : ((int)G.steps.size() + G.depth - 1) / G.depth;
-      if (G.kind == GroupKind::Stencil && nch > 1) {
-        size_t bytes = (size_t)numel(G.shape) * dtype_size(G.dtype);
-        rt.state[0][gi] = dalloc(rt, bytes);
-        if (nch > 2) rt.state[1][gi] = dalloc(rt, bytes);
-      }
+      GroupRT& R = rt.grt[gi];
       if (G.kind == GroupKind::Batch) {
         int64_t tot = 0;
-        rt.batch_offset.clear();
         for (int m : G.batch_members) {
-          rt.batch_offset.push_back(tot);
+          R.offsets.push_back(tot);
           tot += (numel(g.batch_store[m].shape) + 31) / 32 * 32;  // 128-byte aligned slices
-        }
-        if (nch > 1) {
-          rt.batch_state[0] = dalloc(rt, (size_t)tot * dtype_size(G.dtype));
-          if (nch > 2) rt.batch_state[1] = dalloc(rt, (size_t)tot * dtype_size(G.dtype));
         }
       }
       if (!G.reds.empty()) {
-        int slots = 0;
-        if (G.kind == GroupKind::Map) {
-          slots = sms * G.blocks_per_sm;
-        } else {
-          // stencil reductions: one partial per CTA of the last launch
-          int32_t nz, ny, nx;
-          dims3(G.shape, nz, ny, nx);
-          int64_t tiles = (int64_t)((nx + G.tile[2] - 1) / G.tile[2]);
-          if (G.shape.size() >= 2) tiles *= (ny + G.tile[1] - 1) / G.tile[1];
-          if (G.shape.size() == 3) tiles *= (nz + G.tile[0] - 1) / G.tile[0];
-          slots = (int)std::max<int64_t>(1, tiles);
-        }
-        rt.partial_slots[gi] = slots;
-        rt.partials[gi] = dalloc(rt, (size_t)slots * G.reds.size() * 8);
-        rt.tickets[gi] = (unsigned*)dalloc(rt, 256);
-        check_cuda(cudaMemset(rt.tickets[gi], 0, 256), "cudaMemset(ticket)");
+        R.ticket = (unsigned*)dalloc(rt, 256);
+        check_cuda(cudaMemset(R.ticket, 0, 256), "cudaMemset(ticket)");
       }
     }
-    rt.host_tables.assign(rt.launches.size(), nullptr);
-    rt.dev_tables.assign(rt.launches.size(), nullptr);
-    rt.table_tiles.assign(rt.launches.size(), 0);
-    rt.table_key.assign(rt.launches.size(), {});
     check_cuda(cudaEventCreateWithFlags(&rt.table_ev, cudaEventDisableTiming), "cudaEventCreate");
     check_cuda(cudaDeviceSynchronize(), "device set-up");
   } catch (...) {
@@ -261,6 +250,36 @@ static void ensure_device(GraphImpl& g) {
     throw;
   }
   rt.device_ready = true;
+}
+
+// Scratch that depends on the launch shape, allocated on first need.
+static void* group_state(GraphImpl& g, int gi, int which) {
+  auto& rt = *g.rt;
+  GroupRT& R = rt.grt[gi];
+  if (!R.state[which]) {
+    const Group& G = g.groups[gi];
+    size_t elems = 0;
+    if (G.kind == GroupKind::Batch) {
+      for (size_t k = 0; k < G.batch_members.size(); ++k)
+        elems = std::max<size_t>(elems, (size_t)R.offsets[k] +
+                                            (size_t)numel(g.batch_store[G.batch_members[k]].shape));
+    } else {
+      elems = (size_t)numel(G.shape);
+    }
+    R.state[which] = dalloc(rt, elems * dtype_size(G.dtype));
+  }
+  return R.state[which];
+}
+
+static void* group_partials(GraphImpl& g, int gi, int64_t slots) {
+  auto& rt = *g.rt;
+  GroupRT& R = rt.grt[gi];
+  if (slots < 1) slots = 1;
+  if (!R.partials || R.partial_slots < slots) {
+    R.partials = dalloc(rt, (size_t)slots * g.groups[gi].reds.size() * 8);
+    R.partial_slots = (int)slots;
+  }
+  return R.partials;
 }
 
 // ---------------------------------------------------------------------------
@@ -289,8 +308,6 @@ static void launch_map(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
   for (size_t i = 0; i < G.scalars.size(); ++i) p.sc[i] = ptr[G.scalars[i]];
   for (size_t i = 0; i < G.reds.size(); ++i) p.red_out[i] = const_cast<void*>(ptr[G.reds[i]]);
   p.n = numel(G.shape);
-  p.partials = rt.partials[ls.group];
-  p.ticket = rt.tickets[ls.group];
   if (p.n == 0 && G.reds.empty()) return;
   CUfunction fn = ls.fn;
   int per = 16 / (int)esz;
@@ -310,8 +327,13 @@ static void launch_map(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
   int64_t maxb = (int64_t)rt.sms * std::max(1, std::min(G.blocks_per_sm, occ));
   if (blocks > maxb) blocks = maxb;
   if (blocks < 1) blocks = 1;
+  if (!G.reds.empty()) {
+    p.partials = group_partials(g, ls.group, blocks);
+    p.ticket = rt.grt[ls.group].ticket;
+  }
   void* args[] = {&p};
-  check_cu(drv().launchKernel(fn, (unsigned)blocks, 1, 1, G.threads, 1, 1, 0, (CUstream)s, args, nullptr),
+  check_cu(drv().launchKernel(fn, (unsigned)blocks, 1, 1, G.threads, 1, 1, 0, (CUstream)s, args,
+                              nullptr),
            "cuLaunchKernel(map)");
 }
 
@@ -324,6 +346,8 @@ static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const
   const int chunk = ls.s0 / G.depth;
   StParamsH p;
   std::memset(&p, 0, sizeof p);
+  dims3(G.shape, p.nz, p.ny, p.nx);
+  if ((int64_t)p.nz * p.ny * p.nx == 0) return;
   if (first) {
     if (!G.members.empty()) {
       for (size_t i = 0; i < G.loads.size(); ++i) p.ld[i] = ptr[G.loads[i]];
@@ -331,93 +355,138 @@ static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const
       p.ld[0] = ptr[G.st_in];
     }
   } else {
-    p.ld[0] = rt.state[(chunk - 1) % 2][ls.group];
+    p.ld[0] = group_state(g, ls.group, (chunk - 1) % 2);
   }
   if (last) {
     for (size_t i = 0; i < G.stores.size(); ++i) p.st[i] = const_cast<void*>(ptr[G.stores[i]]);
     for (size_t i = 0; i < G.post_loads.size(); ++i) p.pld[i] = ptr[G.post_loads[i]];
     for (size_t i = 0; i < G.reds.size(); ++i) p.red_out[i] = const_cast<void*>(ptr[G.reds[i]]);
   } else {
-    p.st[0] = rt.state[chunk % 2][ls.group];
+    p.st[0] = group_state(g, ls.group, chunk % 2);
   }
   for (size_t i = 0; i < G.scalars.size(); ++i) p.sc[i] = ptr[G.scalars[i]];
-  dims3(G.shape, p.nz, p.ny, p.nx);
-  if ((int64_t)p.nz * p.ny * p.nx == 0) return;
   const int nd = (int)G.shape.size();
-  const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
-  p.tiles_x = (p.nx + TX - 1) / TX;
-  p.tiles_y = (p.ny + TY - 1) / TY;
-  p.tiles_z = nd == 3 ? (p.nz + G.tile[0] - 1) / G.tile[0] : 1;
-  p.partials = rt.partials[ls.group];
-  p.ticket = rt.tickets[ls.group];
-  int64_t gx = (int64_t)p.tiles_x * p.tiles_y;
+  int64_t gx;
+  if (G.variant == 1) {
+    // warp stream: one warp per (strip, row segment) work item, warps stride
+    const int W = stream_width(G);
+    int64_t items = (int64_t)((p.nx + W - 1) / W) * ((p.ny + G.seg - 1) / G.seg);
+    const int wpb = ls.code.threads / 32;
+    int64_t warps = std::min<int64_t>(items, (int64_t)rt.sms * ls.occupancy * wpb);
+    gx = std::max<int64_t>(1, (warps + wpb - 1) / wpb);
+    p.tiles_x = p.tiles_y = p.tiles_z = 1;
+  } else {
+    const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
+    p.tiles_x = (p.nx + TX - 1) / TX;
+    p.tiles_y = (p.ny + TY - 1) / TY;
+    p.tiles_z = nd == 3 ? (p.nz + G.tile[0] - 1) / G.tile[0] : 1;
+    gx = (int64_t)p.tiles_x * p.tiles_y;
+  }
   if (gx > 0x7fffffff) fail(DCP_E_SHAPE, "grid too large");
+  if (last && !G.reds.empty()) {
+    p.partials = group_partials(g, ls.group, gx * p.tiles_z);
+    p.ticket = rt.grt[ls.group].ticket;
+  }
   void* args[] = {&p};
   check_cu(drv().launchKernel(ls.fn, (unsigned)gx, (unsigned)p.tiles_z, 1, ls.code.threads, 1, 1,
-                          ls.code.smem_bytes, (CUstream)s, args, nullptr),
+                              ls.code.smem_bytes, (CUstream)s, args, nullptr),
            "cuLaunchKernel(stencil)");
 }
 
-static void launch_batch(GraphImpl& g, size_t li, LaunchSpec& ls,
-                         const std::vector<const void*>& ptr, cudaStream_t s) {
+static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
+                         cudaStream_t s) {
   auto& rt = *g.rt;
   const Group& G = g.groups[ls.group];
+  GroupRT& R = rt.grt[ls.group];
   const int S = (int)G.steps.size();
   const bool first = ls.s0 == 0, last = ls.s1 == S;
   const int chunk = ls.s0 / G.depth;
   const size_t esz = dtype_size(G.dtype);
   const int nm = (int)G.batch_members.size();
-  // key: the caller pointers this table depends on
+  // the table depends on the caller pointers and on the tile shape
   std::vector<const void*> key;
+  key.push_back((const void*)(intptr_t)G.tile[1]);
+  key.push_back((const void*)(intptr_t)G.tile[2]);
+  key.push_back((const void*)(intptr_t)G.depth);
+  key.push_back((const void*)(intptr_t)G.variant);
   for (int m : G.batch_members) {
     key.push_back(ptr[g.batch_store[m].st_in]);
     key.push_back(ptr[g.batch_store[m].st_out]);
   }
-  if (!rt.dev_tables[li] || rt.table_key[li] != key) {
-    if (!rt.host_tables[li]) {
-      check_cuda(cudaMallocHost((void**)&rt.host_tables[li], sizeof(InstH) * nm), "cudaMallocHost");
-      rt.dev_tables[li] = dalloc(rt, sizeof(InstH) * nm);
-    } else {
+  Table& T = R.tables[chunk];
+  if (!T.dev || T.key != key) {
+    if (!T.host) {
+      check_cuda(cudaMallocHost((void**)&T.host, sizeof(InstH) * nm), "cudaMallocHost");
+      rt.pinned.push_back(T.host);
+      T.dev = dalloc(rt, sizeof(InstH) * nm);
+    } else if (rt.table_ev_used) {
+      // the previous upload of this pinned table must have been consumed
       check_cuda(cudaEventSynchronize(rt.table_ev), "cudaEventSynchronize");
     }
+    const void* in_slab = first ? nullptr : group_state(g, ls.group, (chunk - 1) % 2);
+    void* out_slab = last ? nullptr : group_state(g, ls.group, chunk % 2);
     // members ordered by tile count, largest first, for load balance
-    std::vector<int> order(nm);
-    std::iota(order.begin(), order.end(), 0);
+    // work items of a member: tiles (tile kernel) or column strips (stream kernel)
     auto tiles_of = [&](int k) {
       const Group& M = g.batch_store[G.batch_members[k]];
       int64_t ny = M.shape[0], nx = M.shape[1];
+      if (G.variant == 1) return (nx + stream_width(G) - 1) / stream_width(G);
       return ((nx + G.tile[2] - 1) / G.tile[2]) * ((ny + G.tile[1] - 1) / G.tile[1]);
     };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tiles_of(a) > tiles_of(b); });
+    std::vector<int> order(nm);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return tiles_of(a) > tiles_of(b); });
     int64_t t0 = 0;
     for (int j = 0; j < nm; ++j) {
       int k = order[j];
       const Group& M = g.batch_store[G.batch_members[k]];
-      InstH& I = rt.host_tables[li][j];
-      const size_t off = (size_t)rt.batch_offset[k] * esz;
-      I.in = first ? ptr[M.st_in] : (const char*)rt.batch_state[(chunk - 1) % 2] + off;
-      I.out = last ? const_cast<void*>(ptr[M.st_out]) : (char*)rt.batch_state[chunk % 2] + off;
+      InstH& I = T.host[j];
+      const size_t off = (size_t)R.offsets[k] * esz;
+      I.in = first ? ptr[M.st_in] : (const char*)in_slab + off;
+      I.out = last ? const_cast<void*>(ptr[M.st_out]) : (char*)out_slab + off;
       I.ny = (int32_t)M.shape[0];
       I.nx = (int32_t)M.shape[1];
-      I.tiles_x = (int32_t)((I.nx + G.tile[2] - 1) / G.tile[2]);
+      I.tiles_x = (int32_t)(G.variant == 1 ? tiles_of(k)
+                                           : (I.nx + G.tile[2] - 1) / G.tile[2]);
       I.tile0 = (int32_t)t0;
       t0 += tiles_of(k);
     }
     if (t0 > 0x7fffffff) fail(DCP_E_SHAPE, "batch has too many tiles");
-    rt.table_tiles[li] = (int)t0;
-    check_cuda(cudaMemcpyAsync(rt.dev_tables[li], rt.host_tables[li], sizeof(InstH) * nm,
-                               cudaMemcpyHostToDevice, s),
+    T.tiles = (int)t0;
+    check_cuda(cudaMemcpyAsync(T.dev, T.host, sizeof(InstH) * nm, cudaMemcpyHostToDevice, s),
                "cudaMemcpyAsync(batch table)");
     check_cuda(cudaEventRecord(rt.table_ev, s), "cudaEventRecord");
-    rt.table_key[li] = key;
+    rt.table_ev_used = true;
+    T.key = key;
   }
-  BatchParamsH p{rt.dev_tables[li], nm, rt.table_tiles[li]};
+  BatchParamsH p{T.dev, nm, T.tiles};
   if (p.total_tiles == 0) return;
-  int64_t grid = std::min<int64_t>(p.total_tiles, (int64_t)rt.sms * ls.occupancy);
+  int64_t grid;
+  if (G.variant == 1) {
+    const int wpb = ls.code.threads / 32;
+    grid = std::min<int64_t>((p.total_tiles + wpb - 1) / wpb, (int64_t)rt.sms * ls.occupancy);
+  } else {
+    grid = std::min<int64_t>(p.total_tiles, (int64_t)rt.sms * ls.occupancy);
+  }
   void* args[] = {&p};
-  check_cu(drv().launchKernel(ls.fn, (unsigned)grid, 1, 1, ls.code.threads, 1, 1, ls.code.smem_bytes,
-                          (CUstream)s, args, nullptr),
+  check_cu(drv().launchKernel(ls.fn, (unsigned)grid, 1, 1, ls.code.threads, 1, 1,
+                              ls.code.smem_bytes, (CUstream)s, args, nullptr),
            "cuLaunchKernel(batch)");
+}
+
+static void launch_one(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
+                       cudaStream_t s) {
+  const Group& G = g.groups[ls.group];
+  if (G.kind == GroupKind::Map) launch_map(g, ls, ptr, s);
+  else if (G.kind == GroupKind::Stencil) launch_stencil(g, ls, ptr, s);
+  else launch_batch(g, ls, ptr, s);
+}
+
+static void launch_group(GraphImpl& g, int gi, const std::vector<const void*>& ptr,
+                         cudaStream_t s) {
+  for (auto& ls : g.rt->launches)
+    if (ls.group == gi) launch_one(g, ls, ptr, s);
 }
 
 static std::vector<const void*> bind(GraphImpl& g, const void* const* inputs,
@@ -440,20 +509,185 @@ static std::vector<const void*> bind(GraphImpl& g, const void* const* inputs,
 }
 
 static void launch_all(GraphImpl& g, const std::vector<const void*>& ptr, cudaStream_t s) {
-  auto& rt = *g.rt;
-  for (size_t li = 0; li < rt.launches.size(); ++li) {
-    LaunchSpec& ls = rt.launches[li];
-    const Group& G = g.groups[ls.group];
-    if (G.kind == GroupKind::Map) launch_map(g, ls, ptr, s);
-    else if (G.kind == GroupKind::Stencil) launch_stencil(g, ls, ptr, s);
-    else launch_batch(g, li, ls, ptr, s);
+  for (auto& ls : g.rt->launches) launch_one(g, ls, ptr, s);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner (DCP_AUTOTUNE).  On the first run every stencil / batch group is
+// timed under candidate (depth, tile) choices on the caller's buffers, in
+// execution order (so its inputs are already valid), and keeps the fastest.
+// All candidates perform identical per-step arithmetic, so the tuning run's
+// outputs are the program's outputs.  Choices are cached per group signature
+// in memory and, if DCP_TUNE_CACHE names a file, on disk.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::array<int, 4>> g_tune_cache;  // signature -> depth, tz, ty, tx
+bool g_tune_loaded = false;
+
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* f = std::getenv("DCP_TUNE_CACHE");
+  if (!f || !*f) return;
+  std::ifstream in(f);
+  std::string key;
+  int d, z, y, x;
+  while (in >> key >> d >> z >> y >> x) g_tune_cache[key] = {d, z, y, x};
+}
+
+void tune_cache_store(const std::string& key, const std::array<int, 4>& v) {
+  g_tune_cache[key] = v;
+  const char* f = std::getenv("DCP_TUNE_CACHE");
+  if (!f || !*f) return;
+  std::ofstream out(f, std::ios::app);
+  out << key << " " << v[0] << " " << v[1] << " " << v[2] << " " << v[3] << "\n";
+}
+
+std::string group_signature(const GraphImpl& g, const Group& G, int device_sms) {
+  std::ostringstream os;
+  os << "sm" << device_sms << "|k" << (int)G.kind << "|t" << G.dtype << "|bc" << G.bc << "|s";
+  if (G.kind == GroupKind::Batch) {
+    int64_t cells = 0;
+    for (int m : G.batch_members) cells += numel(g.batch_store[m].shape);
+    os << "B" << G.batch_members.size() << "x" << cells;
+  } else {
+    for (auto v : G.shape) os << v << "x";
   }
+  os << "|n" << G.steps.size() << "|o";
+  for (auto o : G.offsets) os << o << ",";
+  os << "|p" << G.members.size() << "," << G.post.size() << "," << G.reds.size();
+  for (const StepDesc& s : G.steps) os << "," << s.epi.size();
+  char h[32];
+  std::snprintf(h, sizeof h, "%016" PRIx64, fnv1a(os.str()));
+  return h;
+}
+
+std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
+  std::vector<std::array<int, 4>> c;
+  const int S = (int)G.steps.size();
+  const int nd = group_nd(G);
+  if (nd == 3) {
+    const std::array<int, 3> tiles[] = {{32, 8, 32}, {64, 8, 32}, {16, 8, 32},
+                                        {32, 4, 64}, {32, 16, 32}, {64, 4, 64}};
+    for (const auto& t : tiles) c.push_back({1, t[0], t[1], t[2]});
+    return c;
+  }
+  std::vector<int> depths;
+  for (int d : {1, 2, 3, 4, 5, 8, 10})
+    if (d <= S) depths.push_back(d);
+  std::vector<std::array<int, 2>> tiles;
+  if (nd == 1) tiles = {{1, 256}, {1, 512}, {1, 1024}};
+  else if (G.dtype == DCP_F32) tiles = {{32, 64}, {64, 64}, {16, 128}, {32, 128}, {64, 32}};
+  else tiles = {{32, 32}, {16, 64}, {32, 64}, {64, 32}};
+  for (int d : depths)
+    for (const auto& t : tiles) {
+      int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
+      long smem = 2L * (t[0] + 2 * d * ry) * (t[1] + 2 * d * rx) * dtype_size(G.dtype);
+      if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1]});
+    }
+  // warp-stream variant (tz slot = -1 marks it)
+  for (int d : {1, 2, 3, 4, 5, 6, 8, 10})
+    if (d <= S && stream_eligible(G, d)) c.push_back({d, -1, G.tile[1], G.tile[2]});
+  return c;
+}
+
+void apply_config(GraphImpl& g, int gi, const std::array<int, 4>& cfg) {
+  Group& G = g.groups[gi];
+  G.depth = cfg[0];
+  G.variant = cfg[1] < 0 ? 1 : 0;
+  G.tile[0] = cfg[1] < 0 ? 1 : cfg[1];
+  G.tile[1] = cfg[2];
+  G.tile[2] = cfg[3];
+  if (G.variant == 1) {
+    G.threads = 128;
+    if (G.kind != GroupKind::Batch) {
+      int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1, nx = G.shape.back();
+      int64_t strips = (nx + stream_width(G) - 1) / stream_width(G);
+      int64_t seg = std::max<int64_t>((ny * strips + 2431) / 2432, 8 * G.depth * std::max(1, G.radius[1]));
+      G.seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), std::max<int64_t>(ny, 1));
+    }
+  } else {
+    G.threads = 256;
+  }
+  std::vector<LaunchSpec> L = build_group_launches(g, gi);
+  for (auto& ls : L) load_launch(ls);
+  auto& all = g.rt->launches;
+  std::vector<LaunchSpec> merged;
+  bool placed = false;
+  for (auto& ls : all) {
+    if (ls.group == gi) {
+      if (!placed) {
+        for (auto& n : L) merged.push_back(std::move(n));
+        placed = true;
+      }
+      continue;
+    }
+    merged.push_back(std::move(ls));
+  }
+  all = std::move(merged);
+  g.rt->grt[gi].tables.clear();
+}
+}  // namespace
+
+static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStream_t s) {
+  auto& rt = *g.rt;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_cache_load();
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  for (int gi = 0; gi < (int)g.groups.size(); ++gi) {
+    const Group& G = g.groups[gi];
+    if (G.kind == GroupKind::Map) {
+      launch_group(g, gi, ptr, s);
+      continue;
+    }
+    std::string key = group_signature(g, G, rt.sms);
+    auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+      apply_config(g, gi, hit->second);
+      launch_group(g, gi, ptr, s);
+      continue;
+    }
+    std::array<int, 4> best = {G.depth, G.variant == 1 ? -1 : G.tile[0], G.tile[1], G.tile[2]};
+    float best_ms = 1e30f;
+    for (const auto& cfg : tune_candidates(G)) {
+      try {
+        apply_config(g, gi, cfg);
+      } catch (const Error&) {
+        continue;  // a candidate that cannot be compiled or made resident is skipped
+      }
+      launch_group(g, gi, ptr, s);  // warm-up (and table upload)
+      check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+      for (int r = 0; r < 3; ++r) launch_group(g, gi, ptr, s);
+      check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+      check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0.f;
+      check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cfg;
+      }
+    }
+    apply_config(g, gi, best);
+    launch_group(g, gi, ptr, s);
+    tune_cache_store(key, best);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g.n_launches = (int)rt.launches.size();
 }
 
 void run_graph(GraphImpl& g, const void* const* inputs, void* const* outputs, cudaStream_t s) {
   ensure_device(g);
   auto& rt = *g.rt;
   std::vector<const void*> ptr = bind(g, inputs, outputs);
+  if ((g.flags & DCP_AUTOTUNE) && !rt.tuned) {
+    autotune(g, ptr, s);
+    rt.tuned = true;
+    return;  // the tuning run computed this run's outputs
+  }
   auto it = g.options.find(DCP_OPT_USE_GRAPH);
   bool use_graph = it != g.options.end() && it->second == 1;
   if (!use_graph) {
@@ -469,7 +703,6 @@ void run_graph(GraphImpl& g, const void* const* inputs, void* const* outputs, cu
       cudaGraphExecDestroy(rt.gexec);
       rt.gexec = nullptr;
     }
-    // run once eagerly so that any table upload happens outside the capture
     launch_all(g, ptr, s);
     cudaStream_t cs = nullptr;
     check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -494,10 +727,47 @@ void run_graph(GraphImpl& g, const void* const* inputs, void* const* outputs, cu
   check_cuda(cudaGraphLaunch(rt.gexec, s), "cudaGraphLaunch");
 }
 
+// Device-visible address of a page-locked host buffer, or nullptr when the
+// buffer is pageable (then it must be staged through device memory).
+static void* mapped_address(const void* host) {
+  if (!host) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
+}
+
 void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* outputs,
                     cudaStream_t s) {
   ensure_device(g);
   auto& rt = *g.rt;
+  // Zero-copy: when every host buffer is page-locked, the kernels read the
+  // inputs and write the outputs in host memory directly (over the chip-to-
+  // chip link on Grace systems), which avoids the staging copies.
+  auto it = g.options.find(DCP_OPT_HOST_ACCESS);
+  const bool allow_direct = it == g.options.end() || it->second != 0;
+  if (allow_direct) {
+    std::vector<const void*> din(g.inputs.size(), nullptr);
+    std::vector<void*> dout(g.outputs.size(), nullptr);
+    bool ok = true;
+    for (size_t i = 0; i < g.inputs.size() && ok; ++i) {
+      if (g.nodes[g.inputs[i]].numel() == 0) continue;
+      din[i] = mapped_address(inputs[i]);
+      ok = din[i] != nullptr;
+    }
+    for (size_t j = 0; j < g.outputs.size() && ok; ++j) {
+      dout[j] = mapped_address(outputs[j]);
+      ok = dout[j] != nullptr || g.nodes[g.outputs[j]].numel() == 0;
+    }
+    if (ok) {
+      run_graph(g, din.data(), dout.data(), s);
+      check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+      return;
+    }
+  }
   if (rt.stage_in.empty() && !g.inputs.empty()) {
     for (int v : g.inputs)
       rt.stage_in.push_back(dalloc(rt, (size_t)g.nodes[v].numel() * dtype_size(g.nodes[v].dtype)));
@@ -551,6 +821,8 @@ std::string describe_plan(const GraphImpl& g) {
        << ", \"steps\": " << G.steps.size() << ", \"depth\": " << G.depth << ", \"tile\": ["
        << G.tile[0] << ", " << G.tile[1] << ", " << G.tile[2] << "]";
     if (G.kind == GroupKind::Batch) os << ", \"instances\": " << G.batch_members.size();
+    if (G.kind != GroupKind::Map)
+      os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg;
     int epi = 0;
     for (const StepDesc& s : G.steps) epi += (int)s.epi.size();
     os << ", \"epilogue_ops\": " << epi << "}";

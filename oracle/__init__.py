@@ -307,12 +307,22 @@ class Program:
         need = 2 if op in BINARY else 1
         if len(ins) != need:
             raise ValueError("%s takes %d operands" % (op, need))
+        shape = n0.shape
         for v in ins:
-            if self.nodes[v].dtype != n0.dtype or self.nodes[v].shape != n0.shape:
-                raise ValueError("operands of one op share dtype and shape")
+            if self.nodes[v].dtype != n0.dtype:
+                raise ValueError("operands of one op share a dtype")
+            s = self.nodes[v].shape
+            if s != shape:
+                # NumPy broadcasting of a 0-axis (scalar) container
+                if s == ():
+                    continue
+                if shape == ():
+                    shape = s
+                    continue
+                raise ValueError("operand shapes differ (only 0-axis operands broadcast)")
         if n0.dtype.startswith("i") and op not in _INT_OK:
             raise ValueError("%s is not defined on integers" % op)
-        self.nodes.append(_Node("map", n0.dtype, n0.shape, op=op, ins=ins, imm=imm))
+        self.nodes.append(_Node("map", n0.dtype, shape, op=op, ins=ins, imm=imm))
         return len(self.nodes) - 1
 
     def stencil(self, v, offsets, weights, bc, steps):
@@ -343,6 +353,13 @@ def _bits(dtype):
     return 32 if dtype == "i32" else 64
 
 
+def _operands(vals, nd):
+    """Operand arrays of a map node, a 0-axis operand broadcast to the node's shape."""
+    ops = [vals[v] for v in nd.ins]
+    ops = [np.array(np.broadcast_to(o, nd.shape)) if o.shape != nd.shape else o for o in ops]
+    return ops[0], (ops[1] if len(ops) > 1 else None)
+
+
 def run(prog: Program, inputs, detail=False):
     """Evaluate every value of ``prog`` in program order.
 
@@ -363,12 +380,11 @@ def run(prog: Program, inputs, detail=False):
         if nd.kind == "input":
             continue
         if nd.kind == "map":
-            a = vals[nd.ins[0]]
-            b = vals[nd.ins[1]] if len(nd.ins) > 1 else None
+            a, b = _operands(vals, nd)
             if _is_int(nd.dtype):
-                vals[h] = map_i(nd.op, _bits(nd.dtype), a, b, int(nd.imm))
+                vals[h] = map_i(nd.op, _bits(nd.dtype), a, b, int(nd.imm)).reshape(nd.shape)
             else:
-                vals[h] = map_f(nd.op, a, b, nd.imm)
+                vals[h] = map_f(nd.op, a, b, nd.imm).reshape(nd.shape)
         elif nd.kind == "stencil":
             vals[h] = stencil(vals[nd.ins[0]], nd.offsets, nd.weights, nd.bc, nd.steps)
         elif nd.kind == "reduce":
@@ -412,12 +428,15 @@ def adjoint(prog: Program, inputs, out_grads):
         if _is_int(nd.dtype):
             raise ValueError("integer programs have no adjoint")
         if nd.kind == "map":
-            a = vals[nd.ins[0]]
-            b = vals[nd.ins[1]] if len(nd.ins) > 1 else None
+            a, b = _operands(vals, nd)
             ga, gb = map_vjp(nd.op, a, b, nd.imm, vals[h], g)
-            acc(nd.ins[0], ga)
-            if b is not None:
-                acc(nd.ins[1], gb)
+            # a broadcast 0-axis operand receives the sum of its cotangents
+            for v, gv in zip(nd.ins, (ga, gb)):
+                if gv is None:
+                    continue
+                if prog.nodes[v].shape != nd.shape:
+                    gv = np.array(fsum(gv))
+                acc(v, gv.reshape(prog.nodes[v].shape))
         elif nd.kind == "stencil":
             acc(nd.ins[0], stencil_vjp(g, nd.offsets, nd.weights, nd.bc, nd.steps))
         elif nd.kind == "reduce":
@@ -444,10 +463,11 @@ def jvp(prog: Program, inputs, tangents):
         if nd.kind == "input":
             continue
         if nd.kind == "map":
-            a = vals[nd.ins[0]]
-            b = vals[nd.ins[1]] if len(nd.ins) > 1 else None
-            db = tans[nd.ins[1]] if len(nd.ins) > 1 else None
-            tans[h] = map_jvp(nd.op, a, b, nd.imm, vals[h], tans[nd.ins[0]], db)
+            a, b = _operands(vals, nd)
+            ta = np.array(np.broadcast_to(tans[nd.ins[0]], nd.shape))
+            tb = (np.array(np.broadcast_to(tans[nd.ins[1]], nd.shape))
+                  if len(nd.ins) > 1 else None)
+            tans[h] = map_jvp(nd.op, a, b, nd.imm, vals[h], ta, tb).reshape(nd.shape)
         elif nd.kind == "stencil":
             # the step is linear in its input, so its tangent map is the step itself
             tans[h] = stencil(tans[nd.ins[0]], nd.offsets, nd.weights, nd.bc, nd.steps)

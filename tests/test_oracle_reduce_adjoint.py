@@ -230,3 +230,43 @@ def test_linear_stencil_loss_gradient_closed_form():
     p.output(p.reduce(p.map("square", [s]), "sum"))
     (g,) = oracle.adjoint(p, [u0], [1.0])
     assert np.max(np.abs(g - 2 * lam ** (2 * T) * u0)) < 1e-13
+
+
+def test_scalar_operand_broadcast_values():
+    """A 0-axis operand broadcasts like NumPy (hand-derived values; the
+    non-commutative ops catch a swapped operand)."""
+    p = oracle.Program()
+    x = p.input("f64", (3,))
+    s = p.input("f64", ())
+    outs = [p.map("sub", [x, s]), p.map("sub", [s, x]), p.map("div", [s, x]),
+            p.map("mul", [x, s]), p.map("max", [s, x])]
+    for o in outs:
+        p.output(o)
+    vals = oracle.run(p, [np.array([1.0, 2.0, 4.0]), np.array(2.0)])
+    got = [vals[o].tolist() for o in outs]
+    assert got == [[-1.0, 0.0, 2.0], [1.0, 0.0, -2.0], [2.0, 1.0, 0.5], [2.0, 4.0, 8.0],
+                   [2.0, 2.0, 4.0]]
+
+
+def test_broadcast_adjoint_central_differences():
+    """y = (x - mean(x)) / max|x|, loss = sum(y^2): gradient through 0-axis
+    operands checked against central differences."""
+    n = 40
+    p = oracle.Program()
+    x = p.input("f64", (n,))
+    mean = p.map("mul_s", [p.reduce(x, "sum")], 1.0 / n)
+    y = p.map("mul", [p.map("sub", [x, mean]), p.map("add_s", [p.reduce(x, "sum")], 3.0)])
+    p.output(p.reduce(p.map("square", [y]), "sum"))
+    rng = np.random.default_rng(29)
+    x0 = rng.normal(size=n)
+    (g,) = oracle.adjoint(p, [x0], [1.0])
+    eps = 1e-6
+    for i in range(n):
+        up, dn = x0.copy(), x0.copy()
+        up[i] += eps
+        dn[i] -= eps
+        fd = (float(oracle.run(p, [up])[-1]) - float(oracle.run(p, [dn])[-1])) / (2 * eps)
+        assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(fd)), i
+    d = rng.normal(size=n)
+    (jv,) = oracle.jvp(p, [x0], [d])
+    assert abs(float(jv) - float(np.sum(g * d))) < 1e-10 * max(1.0, abs(float(jv)))

@@ -239,7 +239,7 @@ class Stencil(Workload):
     """Iterated stencil workloads; bytes follow the per-step convention
     (every step reads and writes the whole grid once: 2 * T * cells * size)."""
 
-    def __init__(self, name):
+    def __init__(self, name, n=None):
         self.name = name
         import numpy as np
         if name == "jacobi2d":
@@ -248,6 +248,8 @@ class Stencil(Workload):
             self.shape, self.T, self.bc, self.dtype = (512, 512, 512), 50, "periodic", "f64"
         else:
             raise SystemExit("unknown workload %s" % name)
+        if n:  # smaller grid of the same program (profiling)
+            self.shape = (n,) * len(self.shape)
         self.cells = int(np.prod(self.shape))
         self.size = 8
         self.bytes = 2 * self.T * self.cells * self.size
@@ -272,13 +274,18 @@ class Stencil(Workload):
     def setup(self, torch, dev):
         from paper_2107_00555_gb300 import _capi as C
         from paper_2107_00555_gb300 import inputs, programs
-        self.host = [inputs.cfg1() if self.name == "jacobi2d" else inputs.cfg3()]
+        if self.name == "jacobi2d":
+            self.host = [inputs.cfg1(n=self.shape[0])]
+        else:
+            self.host = [inputs.cfg3(n=self.shape[0])]
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         build = programs.jacobi2d if self.name == "jacobi2d" else programs.heat3d
         self.g = build(self.shape, self.T, self.bc, self.dtype)
         if self.name == "jacobi2d":
             self.g.set_option(C.DCP_OPT_USE_GRAPH, 1)
-        self.g.fuse(C.DCP_FUSE_ALL)
+        # tile shape, depth and kernel form picked by the autotuner on the first
+        # (warm-up) run
+        self.g.fuse(C.DCP_FUSE_ALL | C.DCP_AUTOTUNE)
         self.g0 = build(self.shape, self.T, self.bc, self.dtype, fuse=0)
         self.out = self.g.empty_outputs(dev)
         self.out0 = self.g0.empty_outputs(dev)
@@ -371,22 +378,25 @@ class Batch(Workload):
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         self.g = programs.batch2d(self.sides, self.T, "zero", "f32")
         self.g.set_option(C.DCP_OPT_USE_GRAPH, 1)
-        self.g.fuse(C.DCP_FUSE_ALL | C.DCP_BATCH)
+        # autotuned kernel form, depth and work-item size (first warm-up run)
+        self.g.fuse(C.DCP_FUSE_ALL | C.DCP_BATCH | C.DCP_AUTOTUNE)
         self.out = self.g.empty_outputs(dev)
         self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
         self.n_launch = len(self.kernels)
+        # 8192 buffers: marshal them once so a step is one C call
+        self.call = self.g.prepare(self.dev, self.out)
         # comparison forms: every instance as its own fused program, and op by op
         self.g1 = programs.batch2d(self.sides, self.T, "zero", "f32", fuse=C.DCP_FUSE_ALL)
         self.g0 = programs.batch2d(self.sides, self.T, "zero", "f32", fuse=0)
-        self.out1 = self.g1.empty_outputs(dev)
-        self.out0 = self.g0.empty_outputs(dev)
+        self.call1 = self.g1.prepare(self.dev)
+        self.call0 = self.g0.prepare(self.dev)
 
     def step(self):
-        self.g.run(self.dev, self.out)
+        self.call()
 
     def legs(self):
-        return [("unbatched_fused", lambda: self.g1.run(self.dev, self.out1), self.g1.n_kernels),
-                ("op_by_op", lambda: self.g0.run(self.dev, self.out0), self.g0.n_kernels)]
+        return [("unbatched_fused", self.call1, self.g1.n_kernels),
+                ("op_by_op", self.call0, self.g0.n_kernels)]
 
     def setup_e2e(self, torch):
         self.h2d = self.d2h = None
@@ -412,10 +422,10 @@ class Adjoint(Workload):
     metric = "adjoint steps/s"
     unit = "steps/s"
 
-    def __init__(self, name="tanh_adjoint"):
+    def __init__(self, name="tanh_adjoint", n=None):
         self.name = name
         self.dtype = "f64"
-        self.shape, self.T = (256, 256, 256), 20
+        self.shape, self.T = ((n or 256),) * 3, 20
         self.bytes = None
 
     def value(self, t_step):
@@ -424,7 +434,7 @@ class Adjoint(Workload):
     def roof(self):
         # FP64 ALU bound; count the stencil arithmetic only (13 flops per cell per
         # forward step and per reverse step), tanh and its derivative excluded
-        cells = 256 ** 3
+        cells = self.shape[0] ** 3
         return "alu", 13 * cells * 2 * self.T / max(1, self.n_launch), "flop"
 
     def describe(self):
@@ -435,9 +445,9 @@ class Adjoint(Workload):
     def setup(self, torch, dev):
         from paper_2107_00555_gb300 import _capi as C
         from paper_2107_00555_gb300 import inputs, programs
-        self.host = [inputs.cfg5()]
+        self.host = [inputs.cfg5(n=self.shape[0])]
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
-        self.g = programs.tanh_chain(self.shape, self.T, fuse=C.DCP_FUSE_ALL)
+        self.prog = programs.tanh_chain(self.shape, self.T, fuse=C.DCP_FUSE_ALL)
         self.ones = [torch.ones((), dtype=torch.float64, device=dev)]
         self.grad = [torch.empty_like(self.dev[0])]
         self.kernels = []
@@ -446,7 +456,7 @@ class Adjoint(Workload):
         self.grad0 = [torch.empty_like(self.dev[0])]
 
     def step(self):
-        self.g.adjoint(self.dev, self.ones, self.grad)
+        self.prog.adjoint(self.dev, self.ones, self.grad)
 
     def legs(self):
         return [("op_by_op", lambda: self.g0.adjoint(self.dev, self.ones, self.grad0), None)]
@@ -468,11 +478,11 @@ def make_workload(name, n=None):
     if name in ("map_reduce_f32", "map_reduce_f64"):
         return MapReduce(name[-3:], n or (1 << 26))
     if name in ("jacobi2d", "heat3d"):
-        return Stencil(name)
+        return Stencil(name, n)
     if name == "batch2d":
         return Batch()
     if name == "tanh_adjoint":
-        return Adjoint()
+        return Adjoint(n=n)
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -567,6 +577,11 @@ def run_dcp(args):
     for _ in range(args.warmup):
         wl.step()
     barrier()
+    if hasattr(wl, "g"):
+        # the autotuner may have changed the plan during the warm-up runs
+        plan = wl.g.plan()
+        wl.kernels = [l["kernel"] for l in plan["launches"]] or wl.kernels
+        wl.n_launch = len(plan["launches"]) or wl.n_launch
     with ClockSampler(local) as clk:
         t = _time_device(torch, wl.step, args.steps, stream)
         barrier()

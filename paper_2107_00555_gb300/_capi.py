@@ -46,6 +46,7 @@ DCP_OPT_MAP_BLOCKS_PER_SM = 4
 DCP_OPT_USE_GRAPH = 5
 DCP_OPT_STENCIL_KERNEL = 7
 DCP_OPT_HOST_ACCESS = 8
+DCP_OPT_STREAM_ROWS = 9
 
 _STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("DCP_E_") or k == "DCP_OK"}
 

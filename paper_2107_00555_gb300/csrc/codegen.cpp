@@ -6,6 +6,7 @@
 #include <cinttypes>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <sstream>
 
 #include "dcp_internal.h"
@@ -14,7 +15,31 @@ namespace dcp {
 
 namespace {
 
-std::string var(int v) { return "v" + std::to_string(v); }
+// Variable names in generated code are numbered per kernel in order of first
+// use, not by graph node id, so that structurally identical groups (e.g. the
+// same program on many arrays) generate identical sources and share one
+// compiled module.
+thread_local std::map<int, int>* t_names = nullptr;
+
+struct NameScope {
+  std::map<int, int> names;
+  std::map<int, int>* prev;
+  NameScope() : prev(t_names) { t_names = &names; }
+  ~NameScope() { t_names = prev; }
+};
+
+std::string var(int v) {
+  if (!t_names) return "v" + std::to_string(v);
+  auto it = t_names->find(v);
+  int id;
+  if (it == t_names->end()) {
+    id = (int)t_names->size();
+    (*t_names)[v] = id;
+  } else {
+    id = it->second;
+  }
+  return "v" + std::to_string(id);
+}
 
 std::string imm_literal(int dtype, double imm) {
   char buf[96];
@@ -115,6 +140,7 @@ std::string kname_of(const std::string& src) {
 }  // namespace
 
 CodegenOut gen_map_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
+  NameScope names;
   std::ostringstream os;
   const int T = G.dtype;
   int vec = vec_ok ? 16 / dtype_size(T) : 1;
@@ -199,6 +225,7 @@ std::string epi_body(const GraphImpl& g, const StepDesc& s) {
 
 // Warp-stream form (k_stencil2d_stream.cuh) of a 1-D / 2-D stencil launch.
 static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
+  NameScope names;
   const bool batch = G.kind == GroupKind::Batch;
   const int nd = batch ? 2 : (int)G.shape.size();
   const int T = G.dtype;
@@ -209,15 +236,15 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
   const int NR = 2 * ry + 1;
   const int RXA = rx > 0 ? rx : 1;
   std::ostringstream os;
-  os << "// dcp warp-stream stencil kernel: steps [" << s0 << ", " << s1 << ") of "
-     << G.steps.size() << ", bc " << G.bc << ", " << nd << "-D" << (batch ? ", batched" : "") << "\n";
+  os << "// dcp warp-stream stencil kernel: " << nsteps << " steps per launch, bc " << G.bc << ", "
+     << nd << "-D" << (batch ? ", batched" : "") << "\n";
   os << "#define DCP_T " << dtype_cname(T) << "\n#define DCP_C " << C << "\n";
   os << "#define DCP_THREADS " << G.threads << "\n#define DCP_BC " << G.bc << "\n";
   os << "#define DCP_LAST " << (last ? 1 : 0) << "\n#define DCP_BATCH " << (batch ? 1 : 0) << "\n";
   os << "#define DCP_NSTORE " << (last ? (int)G.stores.size() : 1) << "\n#define DCP_NRED "
      << (last ? (int)G.reds.size() : 0) << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n";
   os << "#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_NSTEPS " << nsteps
-     << "\n#define DCP_SEG " << std::max(1, G.seg) << "\n";
+     << "\n";
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   if (!batch) emit_stencil_io(os, g, G, first, last);
@@ -261,14 +288,15 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
 
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
   if (G.variant == 1) return gen_stream_kernel(g, G, s0, s1);
+  NameScope names;
   const bool batch = G.kind == GroupKind::Batch;
   const int nd = batch ? 2 : (int)G.shape.size();
   const int T = G.dtype;
   const int nsteps = s1 - s0;
   const bool first = s0 == 0, last = s1 == (int)G.steps.size();
   std::ostringstream os;
-  os << "// dcp stencil kernel: steps [" << s0 << ", " << s1 << ") of " << G.steps.size()
-     << ", bc " << G.bc << ", " << nd << "-D" << (batch ? ", batched" : "") << "\n";
+  os << "// dcp stencil kernel: " << nsteps << " steps per launch, bc " << G.bc << ", " << nd
+     << "-D" << (batch ? ", batched" : "") << "\n";
   os << "#define DCP_T " << dtype_cname(T) << "\n";
   os << "#define DCP_THREADS " << G.threads << "\n#define DCP_BC " << G.bc << "\n";
   os << "#define DCP_LAST " << (last ? 1 : 0) << "\n#define DCP_BATCH " << (batch ? 1 : 0) << "\n";

@@ -153,8 +153,9 @@ struct CompiledModule {
   double compile_ms = 0.0;
   bool from_cache = false;
 };
-std::vector<char> nvrtc_compile(const std::string& src, const std::string& name, double* ms,
-                                std::string* log);
+typedef std::shared_ptr<const std::vector<char>> CubinRef;
+CubinRef nvrtc_compile(const std::string& src, const std::string& name, double* ms,
+                       std::string* log);
 CUfunction load_function(const std::string& src, const std::string& name, double* ms, int* regs);
 const char* device_header_source();     // dcp_device.cuh
 const char* kernel_map_source();        // k_map.cuh

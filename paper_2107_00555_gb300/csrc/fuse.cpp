@@ -406,7 +406,9 @@ struct Planner {
     G.variant = var;
     if (var == 1) {
       G.threads = 128;
-      if (G.kind != GroupKind::Batch) {
+      if (G.kind == GroupKind::Batch) {
+        G.seg = 64;  // rows per work item: short, uniform items balance the batch
+      } else {
         // rows per work item: enough items to fill the GPU, and at least
         // 8 * depth * radius rows so warm-up rows stay a small fraction
         int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1;
@@ -417,6 +419,8 @@ struct Planner {
         seg = std::max<int64_t>(seg, 8 * G.depth * std::max(1, G.radius[1]));
         G.seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), std::max<int64_t>(ny, 1));
       }
+      auto so = g.options.find(DCP_OPT_STREAM_ROWS);
+      if (so != g.options.end()) G.seg = (int)so->second;
     }
   }
 

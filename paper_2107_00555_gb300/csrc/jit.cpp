@@ -20,7 +20,7 @@ namespace dcp {
 namespace {
 
 std::mutex g_mu;
-std::unordered_map<uint64_t, std::vector<char>> g_cubins;   // source hash -> cubin
+std::unordered_map<uint64_t, std::shared_ptr<const std::vector<char>>> g_cubins;  // hash -> cubin
 struct Loaded {
   CUcontext ctx;
   CUmodule mod;
@@ -42,8 +42,8 @@ std::string disk_path(uint64_t h) {
 
 }  // namespace
 
-std::vector<char> nvrtc_compile(const std::string& src, const std::string& name, double* ms,
-                                std::string* log_out) {
+CubinRef nvrtc_compile(const std::string& src, const std::string& name, double* ms,
+                       std::string* log_out) {
   uint64_t h = fnv1a(src);
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -59,10 +59,11 @@ std::vector<char> nvrtc_compile(const std::string& src, const std::string& name,
     if (f) {
       std::vector<char> c((std::istreambuf_iterator<char>(f)), std::istreambuf_iterator<char>());
       if (!c.empty()) {
+        auto ref = std::make_shared<const std::vector<char>>(std::move(c));
         std::lock_guard<std::mutex> lk(g_mu);
-        g_cubins[h] = c;
+        g_cubins[h] = ref;
         if (ms) *ms = 0.0;
-        return c;
+        return ref;
       }
     }
   }
@@ -108,9 +109,10 @@ std::vector<char> nvrtc_compile(const std::string& src, const std::string& name,
       std::rename(tmp.c_str(), dp.c_str());
     }
   }
+  auto ref = std::make_shared<const std::vector<char>>(std::move(cubin));
   std::lock_guard<std::mutex> lk(g_mu);
-  g_cubins[h] = cubin;
-  return cubin;
+  g_cubins[h] = ref;
+  return ref;
 }
 
 CUfunction load_function(const std::string& src, const std::string& name, double* ms, int* regs) {
@@ -126,9 +128,9 @@ CUfunction load_function(const std::string& src, const std::string& name, double
       return it->second.fn;
     }
   }
-  std::vector<char> cubin = nvrtc_compile(src, name, ms, nullptr);
+  CubinRef cubin = nvrtc_compile(src, name, ms, nullptr);
   CUmodule mod;
-  check_cu(drv().moduleLoadData(&mod, cubin.data()), "cuModuleLoadData");
+  check_cu(drv().moduleLoadData(&mod, cubin->data()), "cuModuleLoadData");
   CUfunction fn;
   check_cu(drv().moduleGetFunction(&fn, mod, name.c_str()), "cuModuleGetFunction");
   int nregs = 0;

@@ -219,6 +219,7 @@ template <typename T> struct DcpStParamsT {
   T* red_out[DCP_MAXIO];
   int nz, ny, nx;
   int tiles_x, tiles_y, tiles_z;
+  int seg, pad_;            // warp-stream kernels: rows per work item
   typename DcpFin<T>::type* partials;
   unsigned int* ticket;
 };

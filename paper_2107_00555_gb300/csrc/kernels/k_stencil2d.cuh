@@ -186,6 +186,8 @@ struct DcpBatchParams {
   const DcpInst* inst;
   int ninst;
   int total_tiles;
+  int seg;   // unused by the tile form
+  int pad_;
 };
 
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {

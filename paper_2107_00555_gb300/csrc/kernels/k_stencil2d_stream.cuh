@@ -17,7 +17,7 @@
 // the largest arrays first in batched launches).
 //
 // The generated prefix defines DCP_T, DCP_C, DCP_RX, DCP_RY, DCP_NSTEPS,
-// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_SEG,
+// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST,
 // DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
 //   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
@@ -53,7 +53,7 @@ struct DcpItem {
   int y0, y1;    // rows written
 };
 
-template <int L, int P>
+template <int L, int P, bool CHECK>
 __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], int j,
                                                const DcpItem& it, int col0, T (&outv)[C],
                                                bool& out_ok) {
@@ -76,20 +76,36 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
   T v[C];
   dcp_level<L - 1>(up, lf, rt, v);
   const bool row_in = (unsigned)y < (unsigned)it.ny;
+  if (!CHECK) {
+    // every column of the strip lies inside the array (and outside a fixed
+    // ring): only the row, uniform across the warp, needs a test
+    const bool ring_row = DCP_BC == DCP_BC_FIXED_RING && (y < DCP_RY || y >= it.ny - DCP_RY);
+    if (!row_in) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    const int col = col0 + c;
-    const bool in = row_in && (unsigned)col < (unsigned)it.nx;
-    T r;
-    if (!in) {
-      r = (T)0;
-    } else if (DCP_BC == DCP_BC_FIXED_RING &&
-               (y < DCP_RY || y >= it.ny - DCP_RY || col < DCP_RX || col >= it.nx - DCP_RX)) {
-      r = dcp_epi<L - 1>(up[DCP_RY][c]);  // ring cell keeps its value; epilogue still applies
+      for (int c = 0; c < C; ++c) v[c] = (T)0;
+    } else if (ring_row) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = dcp_epi<L - 1>(up[DCP_RY][c]);
     } else {
-      r = dcp_epi<L - 1>(v[c]);
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = dcp_epi<L - 1>(v[c]);
     }
-    v[c] = r;
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int col = col0 + c;
+      const bool in = row_in && (unsigned)col < (unsigned)it.nx;
+      T r;
+      if (!in) {
+        r = (T)0;
+      } else if (DCP_BC == DCP_BC_FIXED_RING &&
+                 (y < DCP_RY || y >= it.ny - DCP_RY || col < DCP_RX || col >= it.nx - DCP_RX)) {
+        r = dcp_epi<L - 1>(up[DCP_RY][c]);  // ring cell keeps its value; epilogue still applies
+      } else {
+        r = dcp_epi<L - 1>(v[c]);
+      }
+      v[c] = r;
+    }
   }
   if constexpr (L < K) {
 #pragma unroll
@@ -101,17 +117,20 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
   }
 }
 
-template <int L, int P>
+template <int L, int P, bool CHECK>
 __device__ __forceinline__ void dcp_levels(T (&ring)[K > 1 ? K : 1][NR][C], int j,
                                            const DcpItem& it, int col0, T (&outv)[C],
                                            bool& out_ok) {
   if constexpr (L <= K) {
-    dcp_level_step<L, P>(ring, j, it, col0, outv, out_ok);
-    dcp_levels<L + 1, P>(ring, j, it, col0, outv, out_ok);
+    dcp_level_step<L, P, CHECK>(ring, j, it, col0, outv, out_ok);
+    dcp_levels<L + 1, P, CHECK>(ring, j, it, col0, outv, out_ok);
   }
 }
 
-constexpr int PD = 4;  // input rows in flight (software prefetch distance)
+// Input rows in flight.  Row j lives in queue slot j mod PD and in ring slot
+// j mod NR; iterations are unrolled by PD so both are compile-time constants
+// and no register holding an outstanding load is ever moved.
+constexpr int PD = NR > 1 ? NR : 2;
 
 template <class Input>
 __device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem& it, int col0,
@@ -125,29 +144,57 @@ __device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem&
   }
 }
 
-// One stream iteration: input row j (phase P = j mod NR).  Row j comes from
-// the head of the prefetch queue; row j + PD is requested before the levels
-// are computed, so its load latency overlaps PD iterations of arithmetic.
-template <int P, class Input, class Output>
+// One stream iteration: input row j, P = j mod PD.  Row j + PD is requested
+// into the slot row j vacates before the levels are computed, so its load
+// latency overlaps PD iterations of arithmetic.
+template <int P, bool CHECK, class Input, class Output>
 __device__ __forceinline__ void dcp_iter(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
                                          const DcpItem& it, int col0, Input& input,
                                          Output& output) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) ring[0][P][c] = q[0][c];
-#pragma unroll
-  for (int k = 0; k + 1 < PD; ++k)
-#pragma unroll
-    for (int c = 0; c < C; ++c) q[k][c] = q[k + 1][c];
-  dcp_fetch_row(q[PD - 1], j + PD, it, col0, input);
+  for (int c = 0; c < C; ++c) ring[0][P % NR][c] = q[P][c];
+  dcp_fetch_row(q[P], j + PD, it, col0, input);
   T outv[C];
   bool out_ok = false;
-  dcp_levels<1, P>(ring, j, it, col0, outv, out_ok);
+  dcp_levels<1, P % NR, CHECK>(ring, j, it, col0, outv, out_ok);
   const int y = j - K * DCP_RY;
   if (out_ok && y >= it.y0 && y < it.y1) output(y, outv);
 }
 
-template <class Input, class Output>
-__device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Output&& output) {
+// Iterations j .. j + (PD - P) - 1 with phases P .. PD-1.
+template <int P, bool CHECK, class Input, class Output>
+__device__ __forceinline__ void dcp_iters(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
+                                          const DcpItem& it, int col0, Input& input,
+                                          Output& output) {
+  if constexpr (P < PD) {
+    dcp_iter<P, CHECK>(ring, q, j, it, col0, input, output);
+    dcp_iters<P + 1, CHECK>(ring, q, j + 1, it, col0, input, output);
+  }
+}
+
+// A single iteration of run-time phase r (alignment and tail).
+template <int P, bool CHECK, class Input, class Output>
+__device__ __forceinline__ void dcp_iter_dyn(int r, T (&ring)[K > 1 ? K : 1][NR][C],
+                                             T (&q)[PD][C], int j, const DcpItem& it, int col0,
+                                             Input& input, Output& output) {
+  if constexpr (P < PD) {
+    if (r == P) dcp_iter<P, CHECK>(ring, q, j, it, col0, input, output);
+    else dcp_iter_dyn<P + 1, CHECK>(r, ring, q, j, it, col0, input, output);
+  }
+}
+
+template <int P, class Input>
+__device__ __forceinline__ void dcp_prefill(T (&q)[PD][C], int j0, const DcpItem& it, int col0,
+                                            Input& input) {
+  if constexpr (P < PD) {
+    // the row in [j0, j0 + PD) that maps to slot P
+    dcp_fetch_row(q[P], j0 + dcp_mod(P - j0, PD), it, col0, input);
+    dcp_prefill<P + 1>(q, j0, it, col0, input);
+  }
+}
+
+template <bool CHECK, class Input, class Output>
+__device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input, Output& output) {
   const int lane = threadIdx.x & 31;
   const int col0 = it.x0 - K * DCP_RX + lane * C;
   T ring[K > 1 ? K : 1][NR][C];
@@ -157,45 +204,32 @@ __device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Out
     for (int d = 0; d < NR; ++d)
 #pragma unroll
       for (int c = 0; c < C; ++c) ring[l][d][c] = (T)0;
+  // Rows before the first streamed row hold zeros: exact ghosts above the
+  // array; inside the array they only feed warm-up rows that are never written.
   int j = it.y0 - K * DCP_RY;
   const int jend = it.y1 + K * DCP_RY;
   T q[PD][C];
-#pragma unroll
-  for (int k = 0; k < PD; ++k) dcp_fetch_row(q[k], j + k, it, col0, input);
-  // Rows before the first streamed row hold zeros: exact ghosts above the
-  // array; inside the array they only feed warm-up rows that are never
-  // written.  Iterations run in groups of NR so that every ring index is a
-  // compile-time constant (phase = j mod NR); first align j to a group start.
-  while (j < jend && dcp_mod(j, NR) != 0) {
-    switch (dcp_mod(j, NR)) {
-      case 1: dcp_iter<1 % NR>(ring, q, j, it, col0, input, output); break;
-      case 2: dcp_iter<2 % NR>(ring, q, j, it, col0, input, output); break;
-      case 3: dcp_iter<3 % NR>(ring, q, j, it, col0, input, output); break;
-      case 4: dcp_iter<4 % NR>(ring, q, j, it, col0, input, output); break;
-      default: break;
-    }
+  dcp_prefill<0>(q, j, it, col0, input);
+  while (j < jend && dcp_mod(j, PD) != 0) {
+    dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
     ++j;
   }
-  for (; j + NR <= jend; j += NR) {
-    dcp_iter<0>(ring, q, j, it, col0, input, output);
-    if constexpr (NR > 1) dcp_iter<1 % NR>(ring, q, j + 1, it, col0, input, output);
-    if constexpr (NR > 2) dcp_iter<2 % NR>(ring, q, j + 2, it, col0, input, output);
-    if constexpr (NR > 3) dcp_iter<3 % NR>(ring, q, j + 3, it, col0, input, output);
-    if constexpr (NR > 4) dcp_iter<4 % NR>(ring, q, j + 4, it, col0, input, output);
-  }
-  for (int r = 0; j < jend; ++j, ++r) {
-    switch (r) {
-      case 0: dcp_iter<0>(ring, q, j, it, col0, input, output); break;
-      case 1: dcp_iter<1 % NR>(ring, q, j, it, col0, input, output); break;
-      case 2: dcp_iter<2 % NR>(ring, q, j, it, col0, input, output); break;
-      case 3: dcp_iter<3 % NR>(ring, q, j, it, col0, input, output); break;
-      default: break;
-    }
-  }
+  for (; j + PD <= jend; j += PD) dcp_iters<0, CHECK>(ring, q, j, it, col0, input, output);
+  for (; j < jend; ++j) dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
+}
+
+// Strips whose columns all lie inside the array (outside a fixed ring) take
+// the path without per-column boundary tests.
+template <class Input, class Output>
+__device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Output&& output) {
+  const int lo = DCP_BC == DCP_BC_FIXED_RING ? DCP_RX : 0;
+  const int first = it.x0 - K * DCP_RX;
+  if (first >= lo && first + SPAN <= it.nx - lo) dcp_stream_impl<false>(it, input, output);
+  else dcp_stream_impl<true>(it, input, output);
 }
 
 #if !DCP_BATCH
-// Single array: items = strips x row segments of DCP_SEG rows.
+// Single array: items = strips x row segments of p.seg rows.
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStParams p) {
   T sc[DCP_ARR(DCP_NSCALAR)];
 #pragma unroll
@@ -205,14 +239,15 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   for (int r = 0; r < DCP_NRED; ++r) acc[r] = dcp_red_init<T>(dcp_red_op(r));
   const int ny = p.ny, nx = p.nx;
   const int strips = (nx + W - 1) / W;
-  const int segs = (ny + DCP_SEG - 1) / DCP_SEG;
+  const int SEG = p.seg > 0 ? p.seg : ny;
+  const int segs = (ny + SEG - 1) / SEG;
   const int items = strips * segs;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
   for (int w = warp; w < items; w += nwarps) {
     const int sg = w / strips, st = w - sg * strips;
-    DcpItem it{nullptr, nullptr, ny, nx, st * W, sg * DCP_SEG, min(ny, (sg + 1) * DCP_SEG)};
+    DcpItem it{nullptr, nullptr, ny, nx, st * W, sg * SEG, min(ny, (sg + 1) * SEG)};
     const int col0 = it.x0 - K * DCP_RX + lane * C;
     dcp_stream(
         it, [&](long long gi) { return dcp_input(p, sc, gi); },
@@ -241,17 +276,20 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #endif
 }
 #else
-// Batched form: items are (instance, strip); instances are ordered largest
-// first by the host; the item of warp w is found by binary search.
+// Batched form: items are (instance, strip, row segment); instances are
+// ordered largest first by the host; the item of warp w is found by binary
+// search over the instances' first item numbers.
 struct DcpInst {
   const T* in;
   T* out;
-  int ny, nx, tiles_x, tile0;  // tiles_x = strips of the instance, tile0 = first item
+  int ny, nx, tiles_x, tile0;  // tiles_x = strips of the instance, tile0 = its first item
 };
 struct DcpBatchParams {
   const DcpInst* inst;
   int ninst;
   int total_tiles;
+  int seg;   // rows per work item
+  int pad_;
 };
 
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
@@ -266,8 +304,9 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
       else hi = mid - 1;
     }
     const DcpInst I = p.inst[lo];
-    const int st = w - I.tile0;
-    DcpItem it{I.in, I.out, I.ny, I.nx, st * W, 0, I.ny};
+    const int t = w - I.tile0;
+    const int sg = t / I.tiles_x, st = t - sg * I.tiles_x;
+    DcpItem it{I.in, I.out, I.ny, I.nx, st * W, sg * p.seg, min(I.ny, (sg + 1) * p.seg)};
     const T* in = I.in;
     T* out = I.out;
     const int col0 = it.x0 - K * DCP_RX + lane * C;

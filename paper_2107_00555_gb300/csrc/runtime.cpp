@@ -39,6 +39,7 @@ struct StParamsH {
   void* red_out[kMaxIO];
   int32_t nz, ny, nx;
   int32_t tiles_x, tiles_y, tiles_z;
+  int32_t seg, pad_;
   void* partials;
   void* ticket;
 };
@@ -51,8 +52,10 @@ struct BatchParamsH {
   const void* inst;
   int32_t ninst;
   int32_t total_tiles;
+  int32_t seg;
+  int32_t pad_;
 };
-static_assert(sizeof(StParamsH) == 5 * kMaxIO * 8 + 24 + 16, "stencil params layout");
+static_assert(sizeof(StParamsH) == 5 * kMaxIO * 8 + 32 + 16, "stencil params layout");
 static_assert(sizeof(InstH) == 32, "instance layout");
 
 struct LaunchSpec {
@@ -375,6 +378,7 @@ static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const
     int64_t warps = std::min<int64_t>(items, (int64_t)rt.sms * ls.occupancy * wpb);
     gx = std::max<int64_t>(1, (warps + wpb - 1) / wpb);
     p.tiles_x = p.tiles_y = p.tiles_z = 1;
+    p.seg = G.seg;
   } else {
     const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
     p.tiles_x = (p.nx + TX - 1) / TX;
@@ -409,6 +413,7 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
   key.push_back((const void*)(intptr_t)G.tile[2]);
   key.push_back((const void*)(intptr_t)G.depth);
   key.push_back((const void*)(intptr_t)G.variant);
+  key.push_back((const void*)(intptr_t)G.seg);
   for (int m : G.batch_members) {
     key.push_back(ptr[g.batch_store[m].st_in]);
     key.push_back(ptr[g.batch_store[m].st_out]);
@@ -430,7 +435,8 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
     auto tiles_of = [&](int k) {
       const Group& M = g.batch_store[G.batch_members[k]];
       int64_t ny = M.shape[0], nx = M.shape[1];
-      if (G.variant == 1) return (nx + stream_width(G) - 1) / stream_width(G);
+      if (G.variant == 1)
+        return ((nx + stream_width(G) - 1) / stream_width(G)) * ((ny + G.seg - 1) / G.seg);
       return ((nx + G.tile[2] - 1) / G.tile[2]) * ((ny + G.tile[1] - 1) / G.tile[1]);
     };
     std::vector<int> order(nm);
@@ -447,7 +453,7 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
       I.out = last ? const_cast<void*>(ptr[M.st_out]) : (char*)out_slab + off;
       I.ny = (int32_t)M.shape[0];
       I.nx = (int32_t)M.shape[1];
-      I.tiles_x = (int32_t)(G.variant == 1 ? tiles_of(k)
+      I.tiles_x = (int32_t)(G.variant == 1 ? (I.nx + stream_width(G) - 1) / stream_width(G)
                                            : (I.nx + G.tile[2] - 1) / G.tile[2]);
       I.tile0 = (int32_t)t0;
       t0 += tiles_of(k);
@@ -460,7 +466,7 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
     rt.table_ev_used = true;
     T.key = key;
   }
-  BatchParamsH p{T.dev, nm, T.tiles};
+  BatchParamsH p{T.dev, nm, T.tiles, G.seg, 0};
   if (p.total_tiles == 0) return;
   int64_t grid;
   if (G.variant == 1) {
@@ -586,9 +592,14 @@ std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
       long smem = 2L * (t[0] + 2 * d * ry) * (t[1] + 2 * d * rx) * dtype_size(G.dtype);
       if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1]});
     }
-  // warp-stream variant (tz slot = -1 marks it)
+  // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item, 0 = planner's)
   for (int d : {1, 2, 3, 4, 5, 6, 8, 10})
-    if (d <= S && stream_eligible(G, d)) c.push_back({d, -1, G.tile[1], G.tile[2]});
+    if (d <= S && stream_eligible(G, d)) {
+      if (G.kind == GroupKind::Batch)
+        for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, 0});
+      else
+        c.push_back({d, -1, 0, 0});
+    }
   return c;
 }
 
@@ -601,7 +612,9 @@ void apply_config(GraphImpl& g, int gi, const std::array<int, 4>& cfg) {
   G.tile[2] = cfg[3];
   if (G.variant == 1) {
     G.threads = 128;
-    if (G.kind != GroupKind::Batch) {
+    if (G.kind == GroupKind::Batch) {
+      G.seg = cfg[2] > 0 ? cfg[2] : 64;
+    } else {
       int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1, nx = G.shape.back();
       int64_t strips = (nx + stream_width(G) - 1) / stream_width(G);
       int64_t seg = std::max<int64_t>((ny * strips + 2431) / 2432, 8 * G.depth * std::max(1, G.radius[1]));
@@ -650,7 +663,8 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
       launch_group(g, gi, ptr, s);
       continue;
     }
-    std::array<int, 4> best = {G.depth, G.variant == 1 ? -1 : G.tile[0], G.tile[1], G.tile[2]};
+    std::array<int, 4> best = {G.depth, G.variant == 1 ? -1 : G.tile[0],
+                               G.variant == 1 ? G.seg : G.tile[1], G.tile[2]};
     float best_ms = 1e30f;
     for (const auto& cfg : tune_candidates(G)) {
       try {

@@ -266,3 +266,19 @@ def test_run_host_pinned_buffers(direct):
         vals = oracle.run(t.p, [x0])
         assert_close(out0.numpy(), vals[t.p.outputs[0]], 1e-5, 3.0, "pinned map")
         assert abs(float(out1) - float(vals[t.p.outputs[1]])) <= 1e-4 * float(np.sum(np.abs(x0)))
+
+
+def test_prepared_call_matches_run():
+    sides = [33, 70]
+    us = [inputs.uniform((s, s), 0.0, 1.0, 43 + s).astype(np.float32) for s in sides]
+    g = Graph()
+    vs = [g.input("f32", u.shape) for u in us]
+    for v in vs:
+        g.output(g.stencil(v, FIVE, [0.2] * 5, "zero", 6))
+    g.fuse(C.DCP_FUSE_ALL | C.DCP_BATCH)
+    d = [to_dev(u) for u in us]
+    call = g.prepare(d)
+    a = [to_host(o).copy() for o in call()]
+    b = [to_host(o) for o in g.run(d)]
+    for x, y in zip(a, b):
+        assert x.tobytes() == y.tobytes()

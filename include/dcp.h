@@ -116,7 +116,10 @@ enum {
   DCP_OPT_STENCIL_KERNEL = 7,  /* 2-D stencils: 0 shared-memory tiles, 1 warp stream */
   DCP_OPT_HOST_ACCESS = 8,     /* dcp_run_host: 1 (default) kernels access page-locked host
                                   buffers directly, 0 always stage through device copies */
-  DCP_OPT_STREAM_ROWS = 9      /* warp-stream stencils: rows per work item (>= 1) */
+  DCP_OPT_STREAM_ROWS = 9,     /* warp-stream stencils: rows per work item (>= 1) */
+  DCP_OPT_TILE_Z = 10,         /* 3-D stencils: planes per CTA (z chunk, 1..1024) */
+  DCP_OPT_STREAM_PREFETCH = 11, /* warp-stream stencils: row windows requested ahead (1..4) */
+  DCP_OPT_STREAM_THREADS = 12  /* warp-stream stencils: threads per CTA (32..1024, multiple of 32; default 64) */
 };
 
 /* ---- graph construction ------------------------------------------------ */

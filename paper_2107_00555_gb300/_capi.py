@@ -47,6 +47,9 @@ DCP_OPT_USE_GRAPH = 5
 DCP_OPT_STENCIL_KERNEL = 7
 DCP_OPT_HOST_ACCESS = 8
 DCP_OPT_STREAM_ROWS = 9
+DCP_OPT_TILE_Z = 10
+DCP_OPT_STREAM_PREFETCH = 11
+DCP_OPT_STREAM_THREADS = 12
 
 _STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("DCP_E_") or k == "DCP_OK"}
 

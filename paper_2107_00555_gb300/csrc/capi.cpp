@@ -349,6 +349,9 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
       case DCP_OPT_MAP_BLOCKS_PER_SM:
       case DCP_OPT_STENCIL_KERNEL:
       case DCP_OPT_STREAM_ROWS:
+      case DCP_OPT_TILE_Z:
+      case DCP_OPT_STREAM_PREFETCH:
+      case DCP_OPT_STREAM_THREADS:
         if (g.fused) fail(DCP_E_STATE, "tiling options must be set before dcp_fuse");
         break;
       case DCP_OPT_USE_GRAPH:
@@ -366,6 +369,9 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
     if (key == DCP_OPT_TILE_Y && (v < 1 || v > 512)) fail(DCP_E_INVALID_ARG, "tile y must be in 1..512");
     if (key == DCP_OPT_MAP_BLOCKS_PER_SM && (v < 1 || v > 32)) fail(DCP_E_INVALID_ARG, "blocks per SM must be 1..32");
     if (key == DCP_OPT_STREAM_ROWS && (v < 1 || v > (1 << 30))) fail(DCP_E_INVALID_ARG, "rows per work item must be >= 1");
+    if (key == DCP_OPT_TILE_Z && (v < 1 || v > 1024)) fail(DCP_E_INVALID_ARG, "tile z must be in 1..1024");
+    if (key == DCP_OPT_STREAM_PREFETCH && (v < 1 || v > 4)) fail(DCP_E_INVALID_ARG, "stream prefetch must be in 1..4");
+    if (key == DCP_OPT_STREAM_THREADS && (v < 32 || v > 1024 || v % 32)) fail(DCP_E_INVALID_ARG, "stream threads must be a multiple of 32 in 32..1024");
     g.options[key] = v;
   });
 }

@@ -125,9 +125,19 @@ std::string red_op_fn(const GraphImpl& g, const std::vector<int>& reds) {
   return os.str();
 }
 
+// Hash of the hand-written skeletons: part of every kernel name, so a name
+// (and the compiled-module caches keyed by the source) changes whenever the
+// skeleton it instantiates changes.
+uint64_t skeleton_hash() {
+  static const uint64_t h = fnv1a(std::string(device_header_source()) + kernel_map_source() +
+                                  kernel_stencil2d_source() + kernel_stencil3d_source() +
+                                  kernel_stream_source());
+  return h;
+}
+
 std::string finish(const std::string& prefix, const std::string& body) {
   char name[64];
-  std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(), fnv1a(body));
+  std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(), fnv1a(body) ^ skeleton_hash());
   return std::string("#define DCP_KNAME ") + name + "\n" + body;
 }
 
@@ -244,7 +254,7 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
   os << "#define DCP_NSTORE " << (last ? (int)G.stores.size() : 1) << "\n#define DCP_NRED "
      << (last ? (int)G.reds.size() : 0) << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n";
   os << "#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_NSTEPS " << nsteps
-     << "\n";
+     << "\n#define DCP_PDM " << G.prefetch << "\n";
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   if (!batch) emit_stencil_io(os, g, G, first, last);
@@ -252,6 +262,25 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
      << C << "], const DCP_T (&lf)[" << NR << "][" << RXA << "], const DCP_T (&rt)[" << NR << "]["
      << RXA << "], DCP_T (&out)[" << C << "]);\n";
   os << "template <int S> __device__ __forceinline__ DCP_T dcp_epi(DCP_T v);\n";
+  // which rows of each step read a neighbour column to the left / right
+  // (only those rows are exchanged between lanes)
+  std::vector<unsigned> lmask(nsteps, 0u), rmask(nsteps, 0u);
+  for (int s = 0; s < nsteps; ++s) {
+    const Node& sn = g.nodes[G.steps[s0 + s].node];
+    for (int k = 0; k < sn.npts(); ++k) {
+      const int row = ry + G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+      if (dx < 0) lmask[s] |= 1u << row;
+      if (dx > 0) rmask[s] |= 1u << row;
+    }
+  }
+  auto mask_fn = [&](const char* name, const std::vector<unsigned>& m) {
+    os << "__device__ __forceinline__ constexpr bool " << name << "(int s, int d) {\n"
+       << "  constexpr unsigned m[" << nsteps << "] = {";
+    for (int s = 0; s < nsteps; ++s) os << (s ? ", " : "") << m[s] << "u";
+    os << "};\n  return (m[s] >> d) & 1u;\n}\n";
+  };
+  mask_fn("dcp_uses_lf", lmask);
+  mask_fn("dcp_uses_rt", rmask);
   for (int s = 0; s < nsteps; ++s) {
     const StepDesc& sd = G.steps[s0 + s];
     const Node& sn = g.nodes[sd.node];
@@ -358,7 +387,7 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     os << "  return acc;\n}\n";
     os << "__device__ __forceinline__ DCP_T dcp_epi3(DCP_T v) {\n" << epi_body(g, sd) << "}\n";
     os << "#include \"k_stencil3d.cuh\"\n";
-    out.smem_bytes = (2 * rz + 1) * PW * PH * dtype_size(T);
+    out.smem_bytes = (2 * rz + 2) * PW * PH * dtype_size(T);
   }
   out.source = finish(batch ? "dcp_batch" : (nd == 3 ? "dcp_st3d" : "dcp_st2d"), os.str());
   out.name = kname_of(out.source);

@@ -128,6 +128,7 @@ struct Group {
   int blocks_per_sm = 4;
   int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
   int seg = 0;                  // warp stream: rows per work item (single arrays)
+  int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
   // batch groups: the member stencil groups (same program, different shapes)
   std::vector<int> batch_members;  // indices into Plan::groups of absorbed groups
   bool absorbed = false;           // this stencil group runs inside a batch group

@@ -405,7 +405,8 @@ struct Planner {
     if (it != g.options.end()) var = (it->second == 1 && stream_eligible(G, G.depth)) ? 1 : 0;
     G.variant = var;
     if (var == 1) {
-      G.threads = 128;
+      G.threads = (int)opt(DCP_OPT_STREAM_THREADS, 64);
+      G.prefetch = (int)opt(DCP_OPT_STREAM_PREFETCH, 1);
       if (G.kind == GroupKind::Batch) {
         G.seg = 64;  // rows per work item: short, uniform items balance the batch
       } else {
@@ -435,9 +436,9 @@ struct Planner {
     depth = std::max(1, std::min(depth, S));
     G.depth = depth;
     if (nd == 3) {
-      G.tile[0] = 32;  // z chunk
-      G.tile[1] = 8;
-      G.tile[2] = 32;
+      G.tile[0] = (int)opt(DCP_OPT_TILE_Z, 32);  // z chunk
+      G.tile[1] = (int)opt(DCP_OPT_TILE_Y, 8);
+      G.tile[2] = (int)opt(DCP_OPT_TILE_X, 32);
       G.threads = 256;
     } else {
       G.tile[0] = 1;

@@ -145,6 +145,9 @@ __device__ __forceinline__ void dcp_reduce_epilogue(T (&acc)[NRED > 0 ? NRED : 1
                                                     unsigned int* ticket) {
   typedef typename DcpFin<T>::type F;
   constexpr int NW = NTHREADS / 32;
+  // blocks are numbered over the whole (x, y) grid
+  const unsigned int nblk = gridDim.x * gridDim.y;
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
   __shared__ T s_w[NRED > 0 ? NRED : 1][NW];
   __shared__ F s_f[NRED > 0 ? NRED : 1][NW];
   __shared__ bool s_last;
@@ -162,11 +165,11 @@ __device__ __forceinline__ void dcp_reduce_epilogue(T (&acc)[NRED > 0 ? NRED : 1
     for (int r = 0; r < NRED; ++r) {
       T v = s_w[r][0];
       for (int w = 1; w < NW; ++w) v = dcp_red_comb(dcp_red_op(r), v, s_w[r][w]);
-      partials[(size_t)r * gridDim.x + blockIdx.x] = (F)v;
+      partials[(size_t)r * nblk + bid] = (F)v;
     }
     __threadfence();
     unsigned int t = atomicAdd(ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == nblk - 1);
   }
   __syncthreads();
   if (!s_last) return;
@@ -174,8 +177,8 @@ __device__ __forceinline__ void dcp_reduce_epilogue(T (&acc)[NRED > 0 ? NRED : 1
 #pragma unroll
   for (int r = 0; r < NRED; ++r) {
     F v = (F)dcp_red_init<T>(dcp_red_op(r));
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NTHREADS)
-      v = dcp_fin_comb(dcp_red_op(r), v, __ldcg(partials + (size_t)r * gridDim.x + b));
+    for (unsigned int b = threadIdx.x; b < nblk; b += NTHREADS)
+      v = dcp_fin_comb(dcp_red_op(r), v, __ldcg(partials + (size_t)r * nblk + b));
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) v = dcp_fin_comb(dcp_red_op(r), v, dcp_shfl_xor(v, m));
     if (lane == 0) s_f[r][warp] = v;

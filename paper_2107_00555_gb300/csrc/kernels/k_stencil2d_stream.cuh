@@ -17,12 +17,14 @@
 // the largest arrays first in batched launches).
 //
 // The generated prefix defines DCP_T, DCP_C, DCP_RX, DCP_RY, DCP_NSTEPS,
-// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST,
+// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_PDM,
 // DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
 //   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
 //                     T (&out)[C])   weighted sum of step L (rows up[RY+dy]),
 //   T    dcp_epi<L>(T v)                 epilogue maps fused after step L
+//   bool dcp_uses_lf(int L, int d), dcp_uses_rt(int L, int d)   (constexpr)
+//        whether step L reads a left / right neighbour column in row d
 //   void dcp_post(const DcpStParams& p, const T* sc, long long i, T v, T* st, T* rv)
 typedef DCP_T T;
 typedef typename DcpFin<T>::type F;
@@ -53,7 +55,10 @@ struct DcpItem {
   int y0, y1;    // rows written
 };
 
-template <int L, int P, bool CHECK>
+// CHECK: the strip reaches outside the array (per-column tests).  ROWS: every
+// row touched by this iteration lies inside the array and outside a fixed
+// ring (no row tests).
+template <int L, int P, bool CHECK, bool ROWS>
 __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], int j,
                                                const DcpItem& it, int col0, T (&outv)[C],
                                                bool& out_ok) {
@@ -65,21 +70,29 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
   for (int d = 0; d < NR; ++d)
 #pragma unroll
     for (int c = 0; c < C; ++c) up[d][c] = ring[l][dcp_mod(P - L * DCP_RY + d - DCP_RY, NR)][c];
+  // neighbour columns from the adjacent lanes, only for the rows the step
+  // reads off-centre
   T lf[NR][RXA], rt[NR][RXA];
 #pragma unroll
   for (int d = 0; d < NR; ++d)
 #pragma unroll
+    for (int q = 0; q < RXA; ++q) lf[d][q] = rt[d][q] = (T)0;
+#pragma unroll
+  for (int d = 0; d < NR; ++d)
+#pragma unroll
     for (int q = 0; q < DCP_RX; ++q) {
-      lf[d][DCP_RX - 1 - q] = __shfl_up_sync(0xffffffffu, up[d][C - 1 - q], 1);
-      rt[d][q] = __shfl_down_sync(0xffffffffu, up[d][q], 1);
+      if (dcp_uses_lf(L - 1, d))
+        lf[d][DCP_RX - 1 - q] = __shfl_up_sync(0xffffffffu, up[d][C - 1 - q], 1);
+      if (dcp_uses_rt(L - 1, d)) rt[d][q] = __shfl_down_sync(0xffffffffu, up[d][q], 1);
     }
   T v[C];
   dcp_level<L - 1>(up, lf, rt, v);
-  const bool row_in = (unsigned)y < (unsigned)it.ny;
+  const bool row_in = ROWS || (unsigned)y < (unsigned)it.ny;
   if (!CHECK) {
     // every column of the strip lies inside the array (and outside a fixed
     // ring): only the row, uniform across the warp, needs a test
-    const bool ring_row = DCP_BC == DCP_BC_FIXED_RING && (y < DCP_RY || y >= it.ny - DCP_RY);
+    const bool ring_row =
+        !ROWS && DCP_BC == DCP_BC_FIXED_RING && (y < DCP_RY || y >= it.ny - DCP_RY);
     if (!row_in) {
 #pragma unroll
       for (int c = 0; c < C; ++c) v[c] = (T)0;
@@ -99,7 +112,8 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
       if (!in) {
         r = (T)0;
       } else if (DCP_BC == DCP_BC_FIXED_RING &&
-                 (y < DCP_RY || y >= it.ny - DCP_RY || col < DCP_RX || col >= it.nx - DCP_RX)) {
+                 ((!ROWS && (y < DCP_RY || y >= it.ny - DCP_RY)) || col < DCP_RX ||
+                  col >= it.nx - DCP_RX)) {
         r = dcp_epi<L - 1>(up[DCP_RY][c]);  // ring cell keeps its value; epilogue still applies
       } else {
         r = dcp_epi<L - 1>(v[c]);
@@ -117,79 +131,80 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
   }
 }
 
-template <int L, int P, bool CHECK>
+template <int L, int P, bool CHECK, bool ROWS>
 __device__ __forceinline__ void dcp_levels(T (&ring)[K > 1 ? K : 1][NR][C], int j,
                                            const DcpItem& it, int col0, T (&outv)[C],
                                            bool& out_ok) {
   if constexpr (L <= K) {
-    dcp_level_step<L, P, CHECK>(ring, j, it, col0, outv, out_ok);
-    dcp_levels<L + 1, P, CHECK>(ring, j, it, col0, outv, out_ok);
+    dcp_level_step<L, P, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
+    dcp_levels<L + 1, P, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
   }
 }
 
 // Input rows in flight.  Row j lives in queue slot j mod PD and in ring slot
-// j mod NR; iterations are unrolled by PD so both are compile-time constants
-// and no register holding an outstanding load is ever moved.
-constexpr int PD = NR > 1 ? NR : 2;
+// j mod NR; PD is a multiple of NR and iterations are unrolled by PD, so both
+// are compile-time constants and no register holding an outstanding load is
+// ever moved.  DCP_PDM row windows are requested ahead.
+constexpr int PD = NR * (NR > 1 ? DCP_PDM : 2 * DCP_PDM);
 
-template <class Input>
+template <bool CHECK, bool ROWS, class Input>
 __device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem& it, int col0,
                                               Input& input) {
+  const long long base = (long long)j * it.nx + col0;
+  const bool row_ok = ROWS || (unsigned)j < (unsigned)it.ny;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    const int col = col0 + c;
-    dst[c] = ((unsigned)j < (unsigned)it.ny && (unsigned)col < (unsigned)it.nx)
-                 ? input((long long)j * it.nx + col)
-                 : (T)0;
+    const bool ok = row_ok && (!CHECK || (unsigned)(col0 + c) < (unsigned)it.nx);
+    dst[c] = ok ? input(base + c) : (T)0;
   }
 }
 
 // One stream iteration: input row j, P = j mod PD.  Row j + PD is requested
 // into the slot row j vacates before the levels are computed, so its load
 // latency overlaps PD iterations of arithmetic.
-template <int P, bool CHECK, class Input, class Output>
+template <int P, bool CHECK, bool ROWS, class Input, class Output>
 __device__ __forceinline__ void dcp_iter(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
                                          const DcpItem& it, int col0, Input& input,
                                          Output& output) {
 #pragma unroll
   for (int c = 0; c < C; ++c) ring[0][P % NR][c] = q[P][c];
-  dcp_fetch_row(q[P], j + PD, it, col0, input);
+  dcp_fetch_row<CHECK, ROWS>(q[P], j + PD, it, col0, input);
   T outv[C];
   bool out_ok = false;
-  dcp_levels<1, P % NR, CHECK>(ring, j, it, col0, outv, out_ok);
+  dcp_levels<1, P % NR, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
   const int y = j - K * DCP_RY;
-  if (out_ok && y >= it.y0 && y < it.y1) output(y, outv);
+  if (ROWS || (out_ok && y >= it.y0 && y < it.y1)) output(y, outv);
 }
 
 // Iterations j .. j + (PD - P) - 1 with phases P .. PD-1.
-template <int P, bool CHECK, class Input, class Output>
+template <int P, bool CHECK, bool ROWS, class Input, class Output>
 __device__ __forceinline__ void dcp_iters(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
                                           const DcpItem& it, int col0, Input& input,
                                           Output& output) {
   if constexpr (P < PD) {
-    dcp_iter<P, CHECK>(ring, q, j, it, col0, input, output);
-    dcp_iters<P + 1, CHECK>(ring, q, j + 1, it, col0, input, output);
+    dcp_iter<P, CHECK, ROWS>(ring, q, j, it, col0, input, output);
+    dcp_iters<P + 1, CHECK, ROWS>(ring, q, j + 1, it, col0, input, output);
   }
 }
 
-// A single iteration of run-time phase r (alignment and tail).
+// A single iteration of run-time phase r (alignment and tail), rows tested.
 template <int P, bool CHECK, class Input, class Output>
 __device__ __forceinline__ void dcp_iter_dyn(int r, T (&ring)[K > 1 ? K : 1][NR][C],
                                              T (&q)[PD][C], int j, const DcpItem& it, int col0,
                                              Input& input, Output& output) {
   if constexpr (P < PD) {
-    if (r == P) dcp_iter<P, CHECK>(ring, q, j, it, col0, input, output);
+    if (r == P) dcp_iter<P, CHECK, false>(ring, q, j, it, col0, input, output);
     else dcp_iter_dyn<P + 1, CHECK>(r, ring, q, j, it, col0, input, output);
   }
 }
 
-template <int P, class Input>
+template <int P, bool CHECK, class Input>
 __device__ __forceinline__ void dcp_prefill(T (&q)[PD][C], int j0, const DcpItem& it, int col0,
                                             Input& input) {
   if constexpr (P < PD) {
     // the row in [j0, j0 + PD) that maps to slot P
-    dcp_fetch_row(q[P], j0 + dcp_mod(P - j0, PD), it, col0, input);
-    dcp_prefill<P + 1>(q, j0, it, col0, input);
+    dcp_fetch_row<CHECK, false>(q[P], j0 + dcp_mod(P - j0, PD), it, col0, input);
+    dcp_prefill<P + 1, CHECK>(q, j0, it, col0, input);
   }
 }
 
@@ -209,13 +224,25 @@ __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input,
   int j = it.y0 - K * DCP_RY;
   const int jend = it.y1 + K * DCP_RY;
   T q[PD][C];
-  dcp_prefill<0>(q, j, it, col0, input);
-  while (j < jend && dcp_mod(j, PD) != 0) {
-    dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
-    ++j;
+  dcp_prefill<0, CHECK>(q, j, it, col0, input);
+  // Iterations [jb0, jb1) touch only rows inside the array (and outside a
+  // fixed ring): level rows j - L*RY for L = 1..K, the fetched row j + PD and
+  // the written row j - K*RY in [y0, y1).  They run without row tests.
+  // One loop with one call site per form keeps the unrolled code small:
+  // PD-aligned groups inside [jb0, jb1) take the unchecked form, every other
+  // iteration (warm-up, alignment, tail) the row-checked one.
+  const int ring_w = DCP_BC == DCP_BC_FIXED_RING ? DCP_RY : 0;
+  const int jb0 = K * DCP_RY + max(it.y0, ring_w);
+  const int jb1 = min(min(it.y1 + K * DCP_RY, it.ny - ring_w + DCP_RY), it.ny - PD);
+  while (j < jend) {
+    if (j >= jb0 && j + PD <= jb1 && dcp_mod(j, PD) == 0) {
+      dcp_iters<0, CHECK, true>(ring, q, j, it, col0, input, output);
+      j += PD;
+    } else {
+      dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
+      ++j;
+    }
   }
-  for (; j + PD <= jend; j += PD) dcp_iters<0, CHECK>(ring, q, j, it, col0, input, output);
-  for (; j < jend; ++j) dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
 }
 
 // Strips whose columns all lie inside the array (outside a fixed ring) take

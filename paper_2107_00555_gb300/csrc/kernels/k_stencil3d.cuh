@@ -1,11 +1,14 @@
 // k_stencil3d.cuh -- skeleton of one step of a 3-D stencil (the 7-point
 // heat-equation form of the paper's benchmarks), streamed through z: a CTA
 // owns a DCP_TY x DCP_TX column of the grid over DCP_TZ consecutive planes
-// and keeps the 2*RZ+1 planes it needs in a shared-memory ring, loading one
-// new plane (with its x/y halo) per output plane.  Each input element is
-// therefore read from device memory about (1 + 2*RZ/TZ) times per step and
-// each output written once.  Step epilogue maps, a prologue on the input and
-// post maps / reductions on the output are spliced in by the generator.
+// and keeps the planes it reads in a shared-memory ring of 2*RZ+2 slots.
+// While plane z is computed from the 2*RZ+1 planes around it, the loads of
+// the next plane (with its x/y halo) are already in flight into registers;
+// the one slot not being read receives them, so a single barrier per plane
+// suffices.  Each input element is read from device memory about
+// (1 + 2*RZ/TZ) times per step and each output written once.  Step epilogue
+// maps, a prologue on the input and post maps / reductions on the output are
+// spliced in by the generator.
 //
 // The generated prefix defines DCP_T, DCP_TX, DCP_TY, DCP_TZ, DCP_RX,
 // DCP_RY, DCP_RZ, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST, DCP_NLOAD,
@@ -25,7 +28,10 @@ typedef typename DcpFin<T>::type F;
 constexpr int DCP_PW = DCP_TX + 2 * DCP_RX;
 constexpr int DCP_PH = DCP_TY + 2 * DCP_RY;
 constexpr int DCP_PLANE = DCP_PW * DCP_PH;
-constexpr int DCP_NP = 2 * DCP_RZ + 1;
+constexpr int DCP_NP = 2 * DCP_RZ + 1;                                     // planes read per output plane
+constexpr int DCP_NSLOT = DCP_NP + 1;                                      // ring slots
+constexpr int DCP_LPT = (DCP_PLANE + DCP_THREADS - 1) / DCP_THREADS;       // plane elements per thread
+constexpr int DCP_CPT = (DCP_TX * DCP_TY + DCP_THREADS - 1) / DCP_THREADS; // output cells per thread
 
 typedef DcpStParamsT<T> DcpStParams;
 
@@ -35,23 +41,26 @@ __device__ __forceinline__ int dcp_wrap(int q, int n) {
   return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ void dcp_load_plane(const DcpStParams& p, const T* sc, T* dst, int gz,
-                                               int y0, int x0) {
-  const int nz = p.nz, ny = p.ny, nx = p.nx;
-  for (int i = threadIdx.x; i < DCP_PLANE; i += DCP_THREADS) {
-    const int ly = i / DCP_PW, lx = i - ly * DCP_PW;
-    int z = gz, y = y0 + ly, x = x0 + lx;
-    T v = (T)0;
-    if (DCP_BC == DCP_BC_PERIODIC) {
-      z = dcp_wrap(z, nz);
-      y = dcp_wrap(y, ny);
-      x = dcp_wrap(x, nx);
-      v = dcp_input(p, sc, ((long long)z * ny + y) * nx + x);
-    } else if ((unsigned)z < (unsigned)nz && (unsigned)y < (unsigned)ny &&
-               (unsigned)x < (unsigned)nx) {
-      v = dcp_input(p, sc, ((long long)z * ny + y) * nx + x);
-    }
-    dst[i] = v;
+// Plane gz of the CTA's column (with halo) into registers; off[k] is the
+// in-plane offset of this thread's k-th element, -1 outside the array.
+__device__ __forceinline__ void dcp_fetch_plane(const DcpStParams& p, const T* sc,
+                                                const long long (&off)[DCP_LPT], int gz,
+                                                T (&v)[DCP_LPT]) {
+  int z = gz;
+  bool zok = true;
+  if (DCP_BC == DCP_BC_PERIODIC) z = dcp_wrap(gz, p.nz);
+  else zok = (unsigned)gz < (unsigned)p.nz;
+  const long long zb = (long long)z * p.ny * p.nx;
+#pragma unroll
+  for (int k = 0; k < DCP_LPT; ++k)
+    v[k] = (zok && off[k] >= 0) ? dcp_input(p, sc, zb + off[k]) : (T)0;
+}
+
+__device__ __forceinline__ void dcp_store_plane(T* dst, const T (&v)[DCP_LPT]) {
+#pragma unroll
+  for (int k = 0; k < DCP_LPT; ++k) {
+    const int i = threadIdx.x + k * DCP_THREADS;
+    if (DCP_PLANE % DCP_THREADS == 0 || i < DCP_PLANE) dst[i] = v[k];
   }
 }
 
@@ -71,16 +80,43 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #pragma unroll
   for (int r = 0; r < DCP_NRED; ++r) acc[r] = dcp_red_init<T>(dcp_red_op(r));
 
-  // ring slot of plane z: (z - z0 + RZ) mod NP
-  for (int dz = -DCP_RZ; dz < DCP_RZ; ++dz)
-    dcp_load_plane(p, sc, ring + ((dz + DCP_RZ) % DCP_NP) * DCP_PLANE, z0 + dz, y0, x0);
+  // in-plane offsets of this thread's plane elements (the same for every plane)
+  long long off[DCP_LPT];
+#pragma unroll
+  for (int k = 0; k < DCP_LPT; ++k) {
+    const int i = threadIdx.x + k * DCP_THREADS;
+    const int ly = i / DCP_PW, lx = i - ly * DCP_PW;
+    int y = y0 + ly, x = x0 + lx;
+    bool ok = i < DCP_PLANE;
+    if (DCP_BC == DCP_BC_PERIODIC) {
+      y = dcp_wrap(y, ny);
+      x = dcp_wrap(x, nx);
+    } else {
+      ok = ok && (unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx;
+    }
+    off[k] = ok ? (long long)y * nx + x : -1;
+  }
+
+  // ring slot of plane z: (z - z0 + RZ) mod NSLOT
+  T pf[DCP_LPT];
+  for (int dz = -DCP_RZ; dz < DCP_RZ; ++dz) {
+    dcp_fetch_plane(p, sc, off, z0 + dz, pf);
+    dcp_store_plane(ring + ((dz + DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf);
+  }
+  dcp_fetch_plane(p, sc, off, z0 + DCP_RZ, pf);
   for (int z = z0; z < z1; ++z) {
-    dcp_load_plane(p, sc, ring + ((z - z0 + 2 * DCP_RZ) % DCP_NP) * DCP_PLANE, z + DCP_RZ, y0, x0);
+    // plane z + RZ goes into the slot last read while computing plane z - 2,
+    // which every thread finished before the previous barrier
+    dcp_store_plane(ring + ((z - z0 + 2 * DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf);
+    if (z + 1 < z1) dcp_fetch_plane(p, sc, off, z + DCP_RZ + 1, pf);
     __syncthreads();
     const T* pl[DCP_NP];
 #pragma unroll
-    for (int j = 0; j < DCP_NP; ++j) pl[j] = ring + ((z - z0 + j) % DCP_NP) * DCP_PLANE;
-    for (int i = threadIdx.x; i < DCP_TX * DCP_TY; i += DCP_THREADS) {
+    for (int j = 0; j < DCP_NP; ++j) pl[j] = ring + ((z - z0 + j) % DCP_NSLOT) * DCP_PLANE;
+#pragma unroll
+    for (int k = 0; k < DCP_CPT; ++k) {
+      const int i = threadIdx.x + k * DCP_THREADS;
+      if ((DCP_TX * DCP_TY) % DCP_THREADS != 0 && i >= DCP_TX * DCP_TY) break;
       const int ty = i / DCP_TX, tx = i - ty * DCP_TX;
       const int gy = tyi * DCP_TY + ty, gx = txi * DCP_TX + tx;
       if (gy >= ny || gx >= nx) continue;
@@ -106,7 +142,6 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
       p.st[0][gi] = v;
 #endif
     }
-    __syncthreads();
   }
 #if DCP_LAST && DCP_NRED > 0
   dcp_reduce_epilogue<T, DCP_NRED, DCP_THREADS>(acc, p.red_out, p.partials, p.ticket);

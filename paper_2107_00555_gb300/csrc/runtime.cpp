@@ -592,14 +592,16 @@ std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
       long smem = 2L * (t[0] + 2 * d * ry) * (t[1] + 2 * d * rx) * dtype_size(G.dtype);
       if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1]});
     }
-  // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item, 0 = planner's)
+  // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item,
+  // 0 = planner's; tx slot = row windows requested ahead)
   for (int d : {1, 2, 3, 4, 5, 6, 8, 10})
-    if (d <= S && stream_eligible(G, d)) {
-      if (G.kind == GroupKind::Batch)
-        for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, 0});
-      else
-        c.push_back({d, -1, 0, 0});
-    }
+    if (d <= S && stream_eligible(G, d))
+      for (int pf : {1, 2}) {
+        if (G.kind == GroupKind::Batch)
+          for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf});
+        else
+          c.push_back({d, -1, 0, pf});
+      }
   return c;
 }
 
@@ -611,7 +613,9 @@ void apply_config(GraphImpl& g, int gi, const std::array<int, 4>& cfg) {
   G.tile[1] = cfg[2];
   G.tile[2] = cfg[3];
   if (G.variant == 1) {
-    G.threads = 128;
+    auto th = g.options.find(DCP_OPT_STREAM_THREADS);
+    G.threads = th == g.options.end() ? 64 : (int)th->second;
+    G.prefetch = cfg[3] > 0 ? cfg[3] : 1;
     if (G.kind == GroupKind::Batch) {
       G.seg = cfg[2] > 0 ? cfg[2] : 64;
     } else {
@@ -664,7 +668,8 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
       continue;
     }
     std::array<int, 4> best = {G.depth, G.variant == 1 ? -1 : G.tile[0],
-                               G.variant == 1 ? G.seg : G.tile[1], G.tile[2]};
+                               G.variant == 1 ? G.seg : G.tile[1],
+                               G.variant == 1 ? G.prefetch : G.tile[2]};
     float best_ms = 1e30f;
     for (const auto& cfg : tune_candidates(G)) {
       try {
@@ -836,7 +841,8 @@ std::string describe_plan(const GraphImpl& g) {
        << G.tile[0] << ", " << G.tile[1] << ", " << G.tile[2] << "]";
     if (G.kind == GroupKind::Batch) os << ", \"instances\": " << G.batch_members.size();
     if (G.kind != GroupKind::Map)
-      os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg;
+      os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
+         << ", \"prefetch\": " << G.prefetch;
     int epi = 0;
     for (const StepDesc& s : G.steps) epi += (int)s.epi.size();
     os << ", \"epilogue_ops\": " << epi << "}";

@@ -77,6 +77,9 @@ def test_unknown_fuse_flag_and_options():
     assert _err(g.set_option, 999, 1) == C.DCP_E_INVALID_ARG
     assert _err(g.set_option, C.DCP_OPT_TIME_TILE_DEPTH, 0) == C.DCP_E_INVALID_ARG
     assert _err(g.set_option, C.DCP_OPT_TILE_X, 12) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, C.DCP_OPT_TILE_Z, 0) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, C.DCP_OPT_TILE_Z, 1025) == C.DCP_E_INVALID_ARG
+    g.set_option(C.DCP_OPT_TILE_Z, 16)
     g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 3)
     g.fuse(0)
     assert _err(g.set_option, C.DCP_OPT_TIME_TILE_DEPTH, 2) == C.DCP_E_STATE
@@ -189,3 +192,13 @@ def test_stencil_kernels_compile(bc, shape):
         g.output(g.reduce(g.map("square", [t]), "sum"))
         g.output(t)
         g.fuse(C.DCP_FUSE_ALL)
+
+
+def test_plan_3d_tile_options():
+    g = programs.heat3d((40, 24, 64), 2, "periodic", "f64")
+    g.set_option(C.DCP_OPT_TILE_Z, 16)
+    g.set_option(C.DCP_OPT_TILE_Y, 4)
+    g.set_option(C.DCP_OPT_TILE_X, 64)
+    g.fuse(C.DCP_FUSE_ALL)
+    (grp,) = [x for x in g.plan()["groups"] if x["kind"] == "stencil"]
+    assert grp["tile"] == [16, 4, 64]

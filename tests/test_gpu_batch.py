@@ -101,3 +101,30 @@ def test_graph_replay_and_rebinding():
         ref = oracle.run(OP.jacobi2d(u.shape, 8, "zero", "f32"), [u])[-1]
         assert_close(a, ref, 1e-5, 1.0, "replay")
         assert_close(to_host(b), 2 * ref, 1e-5, 2.0, "rebound")
+
+
+@pytest.mark.parametrize("kernel,depth,prefetch,threads,rows", [
+    (0, 4, 1, 128, 64), (1, 1, 1, 128, 64), (1, 4, 1, 128, 32), (1, 5, 2, 64, 128),
+    (1, 8, 2, 128, 64), (1, 6, 1, 32, 1)])
+def test_batch_kernel_forms_bitwise(kernel, depth, prefetch, threads, rows):
+    """Every kernel form, depth, prefetch depth, CTA size and work-item size
+    of the batched launch gives the bits of one-at-a-time one-step runs."""
+    sides = [1, 3, 40, 97, 128, 200, 33]
+    T = 20
+    us = [inputs.uniform((s, s), 0.0, 1.0, 70 + i, np.float32) for i, s in enumerate(sides)]
+    g = programs.batch2d(sides, T, "zero", "f32")
+    g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+    g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+    g.set_option(C.DCP_OPT_STREAM_PREFETCH, prefetch)
+    g.set_option(C.DCP_OPT_STREAM_THREADS, threads)
+    g.set_option(C.DCP_OPT_STREAM_ROWS, rows)
+    g.fuse(BATCH)
+    (grp,) = g.plan()["groups"]
+    assert grp["kernel_form"] == ("stream" if kernel == 1 else "tile")
+    outs = [to_host(o) for o in g.run([to_dev(u) for u in us])]
+    for u, o in zip(us, outs):
+        g1 = programs.jacobi2d(u.shape, T, "zero", "f32")
+        g1.set_option(C.DCP_OPT_STENCIL_KERNEL, 0)
+        g1.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 1)
+        g1.fuse(C.DCP_FUSE_ALL)
+        assert to_host(g1.run([to_dev(u)])[0]).tobytes() == o.tobytes(), u.shape

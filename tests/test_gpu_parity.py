@@ -170,3 +170,62 @@ def test_jacobi1d_paper_form():
     g.output(g.stencil(v, offs, w, "fixed_ring", 12))
     g.fuse(FUSED)
     assert_close(to_host(g.run([to_dev(u0)])[0]), ref, 1e-12, 1.0, "jacobi1d")
+
+
+@pytest.mark.parametrize("shape", [(70, 20, 28), (100, 9, 33), (33, 40, 65)])
+@pytest.mark.parametrize("tz", [None, 16])
+def test_stencil3d_fused_loss_over_many_z_chunks(shape, tz):
+    """A 3-D stencil chain with a fused reduction whose grid spans several
+    z-chunks: the cross-block pass must number blocks over the whole grid.
+    Repeated runs must agree bitwise (the ticket is reset for the next run)."""
+    T = 3
+    u0 = inputs.uniform(shape, -1.0, 1.0, 31)
+    prog = OP.tanh_chain(shape, T)
+    vals, extra = oracle.run(prog, [u0], detail=True)
+    (lid,) = prog.outputs
+    g = programs.tanh_chain(shape, T)
+    if tz is not None:
+        g.set_option(C.DCP_OPT_TILE_Z, tz)
+        g.set_option(C.DCP_OPT_TILE_Y, 4)
+        g.set_option(C.DCP_OPT_TILE_X, 64)
+    g.fuse(FUSED)
+    plan = g.plan()
+    assert len(plan["launches"]) == T
+    d = to_dev(u0)
+    got = [float(to_host(g.run([d])[0])) for _ in range(3)]
+    assert got[0] == got[1] == got[2]
+    fs, sa = extra[lid]["fsum"], extra[lid]["abs"]
+    assert abs(got[0] - fs) <= 1e-10 * sa, (got[0], fs, sa)
+
+
+@pytest.mark.parametrize("shape", [(1, 1000), (1000, 1), (5, 7), (37, 45), (300, 257), (130, 1030)])
+@pytest.mark.parametrize("bc", ["zero", "fixed_ring"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_stream_kernel_options_bitwise(shape, bc, dtype):
+    """The warp-stream kernel under several depths, prefetch depths, CTA sizes
+    and rows per work item reproduces the one-step tile kernel bit for bit,
+    and the oracle within tolerance."""
+    T = 10
+    u0 = inputs.uniform(shape, 0.0, 1.0, 33, NP[dtype])
+    build = programs.jacobi2d
+    ref = oracle.run(OP.jacobi2d(shape, T, bc), [u0])[-1]
+    g0 = build(shape, T, bc, dtype)
+    g0.set_option(C.DCP_OPT_STENCIL_KERNEL, 0)
+    g0.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 1)
+    g0.fuse(FUSED)
+    base = to_host(g0.run([to_dev(u0)])[0])
+    assert_close(base, ref, tol_for(dtype), float(np.max(u0)), "tile kernel")
+    for depth, pf, th, rows in ((3, 1, 128, None), (5, 2, 64, 17), (10, 2, 32, 1), (4, 4, 256, 300)):
+        g = build(shape, T, bc, dtype)
+        g.set_option(C.DCP_OPT_STENCIL_KERNEL, 1)
+        g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+        g.set_option(C.DCP_OPT_STREAM_PREFETCH, pf)
+        g.set_option(C.DCP_OPT_STREAM_THREADS, th)
+        if rows is not None:
+            g.set_option(C.DCP_OPT_STREAM_ROWS, rows)
+        g.fuse(FUSED)
+        (grp,) = g.plan()["groups"]
+        if grp["kernel_form"] != "stream":
+            continue  # too narrow a strip for this depth: tile kernel chosen
+        got = to_host(g.run([to_dev(u0)])[0])
+        assert got.tobytes() == base.tobytes(), (depth, pf, th, rows)

@@ -157,6 +157,21 @@ dcp_status dcp_add_stencil(dcp_graph g, dcp_value in, int32_t npoints, const int
  * others need >= 1 element (DCP_E_SHAPE otherwise). */
 dcp_status dcp_add_reduce(dcp_graph g, dcp_value in, int32_t red, dcp_value* out);
 
+/* Reduction of `in` along one axis (NumPy `x.sum(axis=axis)`): the
+ * write-conflict-resolution map of Sec. 2.3 / 3.1 whose result keeps one
+ * partial per remaining index (e.g. the row or column sums of a matrix).
+ *   axis   0 <= axis < ndim, or -ndim <= axis < 0 counted from the end
+ *   out    value of the input's shape with `axis` removed (a 1-axis input
+ *          gives a 0-axis value), same dtype
+ * Each output is the reduction of the elements along the axis in index
+ * order up to reassociation (floating sums); integer sums wrap; MAX/MIN
+ * propagate NaN.  SUM along an empty axis gives 0; the others need the axis
+ * to be non-empty (DCP_E_SHAPE otherwise).  Elementwise maps producing `in`
+ * are fused into the reduction kernel.  dcp_run_adjoint does not support
+ * programs containing axis reductions (DCP_E_UNSUPPORTED). */
+dcp_status dcp_add_reduce_axis(dcp_graph g, dcp_value in, int32_t red, int32_t axis,
+                               dcp_value* out);
+
 /* Marks `v` as a program output; outputs bind to dcp_run's `outputs` array
  * in marking order.  An input may not be marked. */
 dcp_status dcp_mark_output(dcp_graph g, dcp_value v);

@@ -26,9 +26,10 @@ Program vocabulary (the oracle's own names):
   applications of ``out[p] = sum_k w_k * in[p + o_k]`` (the jacobi programs of
   Sec. 2.2 and Sec. 4.3), boundary rule ``bc`` in {"zero", "periodic",
   "fixed_ring"}.
-* ``reduce(v, red)`` -- write-conflict resolution of all elements into one
-  scalar (Sec. 2.3, ``alpha += C[i, j]``), ``red`` in {"sum", "max", "min",
-  "maxabs"}.
+* ``reduce(v, red, axis=None)`` -- write-conflict resolution of all elements
+  into one scalar (Sec. 2.3, ``alpha += C[i, j]``), or along one axis with one
+  result per remaining index (``x.sum(axis=a)``), ``red`` in {"sum", "max",
+  "min", "maxabs"}.
 
 ``run`` returns every value; ``adjoint`` runs the reverse pass of the unfused
 program (each op's vector-Jacobian product in reverse order, full tape);
@@ -104,10 +105,13 @@ def _load():
         lib.orc_fsum.restype = D
         lib.orc_reduce_ext_f.argtypes = [I, I64, P, P, P]
         lib.orc_reduce_i.argtypes = [I, I, I64, P, P]
+        lib.orc_reduce_axis_f.argtypes = [I, I64, I64, I64, P, P, P, P]
+        lib.orc_reduce_axis_i.argtypes = [I, I, I64, I64, I64, P, P]
         lib.orc_map_vjp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
         lib.orc_map_jvp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
         for f in (lib.orc_map_f, lib.orc_map_i, lib.orc_stencil_f, lib.orc_stencil_vjp_f,
-                  lib.orc_reduce_ext_f, lib.orc_reduce_i, lib.orc_map_vjp_f, lib.orc_map_jvp_f):
+                  lib.orc_reduce_ext_f, lib.orc_reduce_i, lib.orc_map_vjp_f, lib.orc_map_jvp_f,
+                  lib.orc_reduce_axis_f, lib.orc_reduce_axis_i):
             f.restype = I
         _lib = lib
     return _lib
@@ -243,6 +247,41 @@ def reduce_i(red, bits, y):
     return out.value
 
 
+def _axis_view(shape, axis):
+    nd = len(shape)
+    if not -nd <= axis < nd:
+        raise ValueError("axis %d out of range for %d axes" % (axis, nd))
+    axis %= nd
+    outer = int(np.prod(shape[:axis], dtype=np.int64))
+    inner = int(np.prod(shape[axis + 1:], dtype=np.int64))
+    return axis, outer, int(shape[axis]), inner, tuple(s for d, s in enumerate(shape) if d != axis)
+
+
+def reduce_axis(red, y, axis):
+    """Floating reduction along one axis; for "sum" returns (sequential sum,
+    exactly rounded sum, magnitude sum) per output, else the reduced array."""
+    y = _f64(y)
+    axis, outer, R, inner, oshape = _axis_view(y.shape, axis)
+    out = np.empty(outer * inner)
+    fs = np.empty(outer * inner) if red == "sum" else None
+    ab = np.empty(outer * inner) if red == "sum" else None
+    _check(_load().orc_reduce_axis_f(REDS[red], outer, R, inner, _p(y), _p(out), _p(fs), _p(ab)),
+           red + " along an axis")
+    if red == "sum":
+        return out.reshape(oshape), fs.reshape(oshape), ab.reshape(oshape)
+    return out.reshape(oshape)
+
+
+def reduce_axis_i(red, bits, y, axis):
+    """Integer reduction along one axis (sum wraps modulo 2**bits)."""
+    y = _i64(y)
+    axis, outer, R, inner, oshape = _axis_view(y.shape, axis)
+    out = np.empty(outer * inner, dtype=np.int64)
+    _check(_load().orc_reduce_axis_i(REDS[red], bits, outer, R, inner, _p(y), _p(out)),
+           red + " along an axis")
+    return out.reshape(oshape)
+
+
 def map_vjp(op, a, b, imm, y, g):
     """Adjoints (ga, gb) of one floating map op given its forward output y."""
     lib = _load()
@@ -283,6 +322,7 @@ class _Node:
     weights: object = None
     bc: str = "zero"
     steps: int = 1
+    axis: object = None       # reduce: None = all axes, else the reduced axis
 
 
 @dataclass
@@ -335,9 +375,13 @@ class Program:
                                 steps=int(steps)))
         return len(self.nodes) - 1
 
-    def reduce(self, v, red):
+    def reduce(self, v, red, axis=None):
         n0 = self.nodes[v]
-        self.nodes.append(_Node("reduce", n0.dtype, (), op=red, ins=(v,)))
+        if axis is None:
+            self.nodes.append(_Node("reduce", n0.dtype, (), op=red, ins=(v,)))
+        else:
+            axis, _, _, _, oshape = _axis_view(n0.shape, int(axis))
+            self.nodes.append(_Node("reduce", n0.dtype, oshape, op=red, ins=(v,), axis=axis))
         return len(self.nodes) - 1
 
     def output(self, v):
@@ -387,6 +431,16 @@ def run(prog: Program, inputs, detail=False):
                 vals[h] = map_f(nd.op, a, b, nd.imm).reshape(nd.shape)
         elif nd.kind == "stencil":
             vals[h] = stencil(vals[nd.ins[0]], nd.offsets, nd.weights, nd.bc, nd.steps)
+        elif nd.kind == "reduce" and nd.axis is not None:
+            y = vals[nd.ins[0]]
+            if _is_int(nd.dtype):
+                vals[h] = reduce_axis_i(nd.op, _bits(nd.dtype), y, nd.axis)
+            elif nd.op == "sum":
+                vals[h], fs, ab = reduce_axis("sum", y, nd.axis)
+                if detail:
+                    extra[h] = {"fsum": fs, "abs": ab}
+            else:
+                vals[h] = reduce_axis(nd.op, y, nd.axis)
         elif nd.kind == "reduce":
             y = vals[nd.ins[0]]
             if _is_int(nd.dtype):
@@ -412,6 +466,8 @@ def adjoint(prog: Program, inputs, out_grads):
     Each op's vector-Jacobian product is applied in reverse program order on a
     full tape of forward values; cotangents of values used twice add up.
     """
+    if any(nd.kind == "reduce" and nd.axis is not None for nd in prog.nodes):
+        raise ValueError("the adjoint of axis reductions is not implemented")
     vals = run(prog, inputs)
     grads = [None] * len(prog.nodes)
 
@@ -455,6 +511,8 @@ def adjoint(prog: Program, inputs, out_grads):
 
 def jvp(prog: Program, inputs, tangents):
     """Forward tangent pass: the directional derivative of every output."""
+    if any(nd.kind == "reduce" and nd.axis is not None for nd in prog.nodes):
+        raise ValueError("the tangent of axis reductions is not implemented")
     vals = run(prog, inputs)
     tans = [None] * len(prog.nodes)
     for h, t in zip(prog.inputs, tangents):

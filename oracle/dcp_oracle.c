@@ -508,6 +508,65 @@ int orc_reduce_i(int red, int bits, int64_t n, const int64_t* y, int64_t* out) {
   return 0;
 }
 
+/* Reduction along one axis (NumPy x.sum(axis=a) and friends: the
+ * write-conflict resolution of Sec. 2.3 with one result per remaining index).
+ * y is viewed as (outer, R, inner) in C order; out[o*inner + i] reduces the
+ * R elements y[o, 0..R-1, i], gathered in index order, with the whole-array
+ * routines above: SUM sequentially (fs and ab, when not NULL, receive the
+ * exactly rounded sum and the magnitude sum of each output), MAX / MIN /
+ * MAXABS with NaN propagation (R >= 1). */
+int orc_reduce_axis_f(int red, int64_t outer, int64_t R, int64_t inner, const double* y,
+                      double* out, double* fs, double* ab) {
+  if (red != ORC_RED_SUM && R < 1) return -1;
+  double* col = (double*)malloc(sizeof(double) * (size_t)(R > 0 ? R : 1));
+  if (!col) return -2;
+  for (int64_t o = 0; o < outer; ++o)
+    for (int64_t i = 0; i < inner; ++i) {
+      const int64_t k = o * inner + i;
+      for (int64_t r = 0; r < R; ++r) col[r] = y[(o * R + r) * inner + i];
+      if (red == ORC_RED_SUM) {
+        out[k] = orc_sum_seq(R, col);
+        if (fs) {
+          int st = 0;
+          fs[k] = orc_fsum(R, col, &st);
+          if (st) {
+            free(col);
+            return st;
+          }
+        }
+        if (ab) ab[k] = orc_sum_abs(R, col);
+      } else {
+        int64_t arg = 0;
+        int st = orc_reduce_ext_f(red, R, col, &out[k], &arg);
+        if (st) {
+          free(col);
+          return st;
+        }
+      }
+    }
+  free(col);
+  return 0;
+}
+
+/* Integer reduction along one axis (same view; SUM wraps modulo 2^bits). */
+int orc_reduce_axis_i(int red, int bits, int64_t outer, int64_t R, int64_t inner,
+                      const int64_t* y, int64_t* out) {
+  if (red != ORC_RED_SUM && R < 1) return -1;
+  int64_t* col = (int64_t*)malloc(sizeof(int64_t) * (size_t)(R > 0 ? R : 1));
+  if (!col) return -2;
+  for (int64_t o = 0; o < outer; ++o)
+    for (int64_t i = 0; i < inner; ++i) {
+      for (int64_t r = 0; r < R; ++r) col[r] = y[(o * R + r) * inner + i];
+      int st = orc_reduce_i(red, bits, R, col, &out[o * inner + i]);
+      if (st) {
+        free(col);
+        return st;
+      }
+    }
+  free(col);
+  return 0;
+}
+
 /* ======================================================================= */
 /* Derivatives of the floating-point maps, for the reverse (adjoint) and     */
 /* forward (tangent) passes of the unfused program.                         */

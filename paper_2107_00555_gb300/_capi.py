@@ -82,6 +82,8 @@ _SIG = [
                                          ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     ("dcp_add_reduce", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),
+    ("dcp_add_reduce_axis", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32)]),
     ("dcp_mark_output", ctypes.c_int32, [_P, ctypes.c_int32]),
     ("dcp_fuse", ctypes.c_int32, [_P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
     ("dcp_run", ctypes.c_int32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
@@ -171,6 +173,12 @@ def dcp_add_stencil(g, v, offsets, weights, bc, steps):
 def dcp_add_reduce(g, v, red):
     out = ctypes.c_int32()
     _check("dcp_add_reduce", load().dcp_add_reduce(g, v, red, ctypes.byref(out)))
+    return out.value
+
+
+def dcp_add_reduce_axis(g, v, red, axis):
+    out = ctypes.c_int32()
+    _check("dcp_add_reduce_axis", load().dcp_add_reduce_axis(g, v, red, axis, ctypes.byref(out)))
     return out.value
 
 

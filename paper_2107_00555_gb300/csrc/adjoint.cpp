@@ -380,9 +380,12 @@ struct AdjointPlan {
 };
 
 void plan_adjoint(const GraphImpl& F, size_t budget, AdjointPlan& out) {
-  for (const Node& n : F.nodes)
+  for (const Node& n : F.nodes) {
     if (!dtype_is_float(n.dtype))
       fail(DCP_E_UNSUPPORTED, "the adjoint is defined for floating programs only");
+    if (n.kind == Kind::Reduce && n.axis >= 0)
+      fail(DCP_E_UNSUPPORTED, "the adjoint of axis reductions is not implemented");
+  }
   Planner P(F);
   const int N = P.N;
   // segment boundaries: before every k-th stencil node

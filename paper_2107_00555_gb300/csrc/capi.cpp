@@ -274,6 +274,34 @@ dcp_status dcp_add_reduce(dcp_graph gh, dcp_value vin, int32_t red, dcp_value* o
   });
 }
 
+dcp_status dcp_add_reduce_axis(dcp_graph gh, dcp_value vin, int32_t red, int32_t axis,
+                               dcp_value* out) {
+  return guarded([&] {
+    GraphImpl& g = G(gh);
+    check_mutable(g);
+    if (!out) fail(DCP_E_INVALID_ARG, "out is NULL");
+    const Node& a = value(g, vin);
+    if (red < DCP_SUM || red > DCP_MAXABS) fail(DCP_E_INVALID_ARG, "unknown reduction");
+    const int nd = a.ndim();
+    if (nd == 0) fail(DCP_E_SHAPE, "a 0-axis value has no axis to reduce");
+    if (axis < -nd || axis >= nd)
+      fail(DCP_E_INVALID_ARG, "axis " + std::to_string(axis) + " out of range for " +
+                                  std::to_string(nd) + " axes");
+    if (axis < 0) axis += nd;
+    if (red != DCP_SUM && a.shape[axis] == 0)
+      fail(DCP_E_SHAPE, std::string(red_name(red)) + " along an empty axis is undefined");
+    Node n;
+    n.kind = Kind::Reduce;
+    n.dtype = a.dtype;
+    n.op = red;
+    n.axis = axis;
+    for (int d = 0; d < nd; ++d)
+      if (d != axis) n.shape.push_back(a.shape[d]);
+    n.in.push_back(vin);
+    *out = push(g, std::move(n));
+  });
+}
+
 dcp_status dcp_mark_output(dcp_graph gh, dcp_value v) {
   return guarded([&] {
     GraphImpl& g = G(gh);

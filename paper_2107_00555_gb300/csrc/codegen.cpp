@@ -131,7 +131,7 @@ std::string red_op_fn(const GraphImpl& g, const std::vector<int>& reds) {
 uint64_t skeleton_hash() {
   static const uint64_t h = fnv1a(std::string(device_header_source()) + kernel_map_source() +
                                   kernel_stencil2d_source() + kernel_stencil3d_source() +
-                                  kernel_stream_source());
+                                  kernel_stream_source() + kernel_axis_source());
   return h;
 }
 
@@ -177,6 +177,38 @@ CodegenOut gen_map_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
   os << "#include \"k_map.cuh\"\n";
   CodegenOut out;
   out.source = finish(vec > 1 ? "dcp_map_v" : "dcp_map_s", os.str());
+  out.name = kname_of(out.source);
+  out.threads = G.threads;
+  out.smem_bytes = 0;
+  return out;
+}
+
+// Axis reduction (k_axis.cuh): the reduced operands, with the fused
+// prologue maps, at a flat index of the iteration space.
+CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& G) {
+  NameScope names;
+  std::ostringstream os;
+  const int T = G.dtype;
+  os << "// dcp axis reduction kernel: " << G.members.size() << " prologue ops, " << G.loads.size()
+     << " loads, " << G.reds.size() << " reductions along axis " << G.axis << "\n";
+  os << "#define DCP_T " << dtype_cname(T) << "\n#define DCP_THREADS " << G.threads
+     << "\n#define DCP_NRED " << G.reds.size() << "\n#define DCP_NSCALAR " << G.scalars.size()
+     << "\n";
+  os << red_op_fn(g, G.reds);
+  os << "#include \"dcp_device.cuh\"\n";
+  os << "__device__ __forceinline__ void dcp_elem(const DcpAxParamsT<DCP_T>& p, const DCP_T* sc, "
+        "long long gi, DCP_T* rv) {\n";
+  for (size_t i = 0; i < G.loads.size(); ++i)
+    os << "  const DCP_T " << var(G.loads[i]) << " = p.ld[" << i << "][gi];\n";
+  for (size_t i = 0; i < G.scalars.size(); ++i)
+    os << "  const DCP_T " << var(G.scalars[i]) << " = sc[" << i << "];\n";
+  emit_members(os, g, G.members);
+  for (size_t i = 0; i < G.reds.size(); ++i)
+    os << "  rv[" << i << "] = " << var(g.nodes[G.reds[i]].in[0]) << ";\n";
+  os << "  (void)p; (void)sc; (void)gi;\n}\n";
+  os << "#include \"k_axis.cuh\"\n";
+  CodegenOut out;
+  out.source = finish("dcp_axis", os.str());
   out.name = kname_of(out.source);
   out.threads = G.threads;
   out.smem_bytes = 0;

@@ -64,6 +64,8 @@ struct Node {
   std::vector<double> weights;
   int bc = DCP_BC_ZERO;
   int steps = 0;
+  // reduce: the reduced axis of the operand, -1 = all axes
+  int axis = -1;
   int64_t numel() const {
     int64_t n = 1;
     for (auto s : shape) n *= s;
@@ -91,7 +93,7 @@ const char* red_name(int red);
 // Fused plan (Sec. 3.1: greedy subgraph fusion, tiled write-conflict
 // resolution, transient mitigation).
 // ---------------------------------------------------------------------------
-enum class GroupKind { Map, Stencil, Batch };
+enum class GroupKind { Map, Stencil, Batch, AxisReduce };
 
 // One step of an iterated stencil inside a stencil group.  `node` is the
 // stencil node providing offsets/weights; `epi` the unary/immediate map nodes
@@ -129,6 +131,8 @@ struct Group {
   int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
   int seg = 0;                  // warp stream: rows per work item (single arrays)
   int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
+  // axis-reduce groups: the reduced axis of the iteration space `shape`
+  int axis = -1;
   // batch groups: the member stencil groups (same program, different shapes)
   std::vector<int> batch_members;  // indices into Plan::groups of absorbed groups
   bool absorbed = false;           // this stencil group runs inside a batch group
@@ -163,6 +167,7 @@ const char* kernel_map_source();        // k_map.cuh
 const char* kernel_stencil2d_source();  // k_stencil2d.cuh
 const char* kernel_stencil3d_source();  // k_stencil3d.cuh
 const char* kernel_stream_source();     // k_stencil2d_stream.cuh
+const char* kernel_axis_source();       // k_axis.cuh
 
 // ---------------------------------------------------------------------------
 // Graph object
@@ -217,6 +222,7 @@ CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 // Stencil launch `chunk` covers steps [s0, s1) of the group.
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
 CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
+CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& grp);
 // adjoint kernels
 CodegenOut gen_map_adjoint_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int step);

@@ -54,7 +54,7 @@ struct Planner {
   // Is `v` computed in registers by group `gi` (member, stencil output, post)?
   bool computed_in(int gi, int v) const {
     const Group& G = g.groups[gi];
-    if (G.kind == GroupKind::Map) return in_vec(G.members, v);
+    if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce) return in_vec(G.members, v);
     if (G.kind == GroupKind::Stencil) return v == G.st_out || in_vec(G.post, v);
     return false;
   }
@@ -136,7 +136,7 @@ struct Planner {
         if (G.shape != n.shape) continue;
         if (G.kind == GroupKind::Map && !fmaps()) continue;
         if (G.kind == GroupKind::Stencil && !fsub()) continue;
-        if (G.kind == GroupKind::Batch) continue;
+        if (G.kind == GroupKind::Batch || G.kind == GroupKind::AxisReduce) continue;
         bool ok = true;
         for (int b : n.in)
           if (!computed_in(gi, b) && !available_before(b, gi)) ok = false;
@@ -175,12 +175,84 @@ struct Planner {
     for (int a : n.in) add_operand(g.groups[gi], gi, a);
   }
 
+  // Axis reduction (tiled write-conflict resolution with one partial per
+  // remaining index): joins the axis-reduce group computing its operand, or
+  // the latest one over the same space and axis; otherwise starts a group
+  // that takes the producer map group as its prologue when every value of
+  // that group is consumed inside it or by reductions along the same axis.
+  void plan_axis_reduce(int v) {
+    const Node& n = g.nodes[v];
+    int a = n.in[0];
+    const Node& an = g.nodes[a];
+    auto same_space = [&](const Group& G) {
+      return G.kind == GroupKind::AxisReduce && G.shape == an.shape && G.axis == n.axis &&
+             G.dtype == an.dtype;
+    };
+    int gi = g.value_group[a];
+    if (gi >= 0 && g.groups[gi].kind == GroupKind::AxisReduce && computed_in(gi, a)) {
+      Group& G = g.groups[gi];
+      if (!same_space(G) || (int)G.reds.size() >= kMaxIO)
+        fail(DCP_E_UNSUPPORTED, "too many reductions of one fused prologue");
+      G.reds.push_back(v);
+      g.value_group[v] = gi;
+      return;
+    }
+    if (fsub() && !g.groups.empty()) {
+      int li = (int)g.groups.size() - 1;
+      Group& G = g.groups[li];
+      if (same_space(G) && (int)G.reds.size() < kMaxIO && available_before(a, li)) {
+        G.reds.push_back(v);
+        g.value_group[v] = li;
+        add_operand(G, li, a);
+        return;
+      }
+    }
+    Group R;
+    R.kind = GroupKind::AxisReduce;
+    R.dtype = an.dtype;
+    R.shape = an.shape;
+    R.axis = n.axis;
+    bool absorbed = false;
+    if (fsub() && gi >= 0 && gi == (int)g.groups.size() - 1 &&
+        g.groups[gi].kind == GroupKind::Map && computed_in(gi, a)) {
+      const Group& M = g.groups[gi];
+      bool ok = M.reds.empty() && M.shape == an.shape;
+      int nred = 0;
+      for (int m : M.members) {
+        if (is_out[m] || g.nodes[m].kind != Kind::Map) ok = false;
+        for (int u : users[m]) {
+          if (!live[u] || in_vec(M.members, u)) continue;
+          const Node& un = g.nodes[u];
+          if (un.kind == Kind::Reduce && un.axis == n.axis) ++nred;
+          else ok = false;
+        }
+      }
+      if (ok && nred <= kMaxIO) {
+        R.members = M.members;
+        R.loads = M.loads;
+        R.scalars = M.scalars;
+        g.groups.pop_back();
+        absorbed = true;
+      }
+    }
+    if (!absorbed) R.loads.push_back(a);
+    R.reds.push_back(v);
+    g.groups.push_back(R);
+    int ri = (int)g.groups.size() - 1;
+    g.value_group[v] = ri;
+    for (int m : R.members) g.value_group[m] = ri;
+  }
+
   void plan_reduce(int v) {
     const Node& n = g.nodes[v];
+    if (n.axis >= 0) {
+      plan_axis_reduce(v);
+      return;
+    }
     int a = n.in[0];
     int gi = g.value_group[a];
     if (fsub() && gi >= 0 && computed_in(gi, a) && g.groups[gi].kind != GroupKind::Batch &&
-        (int)g.groups[gi].reds.size() < kMaxIO) {
+        g.groups[gi].kind != GroupKind::AxisReduce && (int)g.groups[gi].reds.size() < kMaxIO) {
       g.groups[gi].reds.push_back(v);
       g.value_group[v] = gi;
       return;
@@ -381,6 +453,9 @@ struct Planner {
       if (G.kind == GroupKind::Map) {
         G.threads = 256;
         G.blocks_per_sm = (int)opt(DCP_OPT_MAP_BLOCKS_PER_SM, 8);
+        nl += 1;
+      } else if (G.kind == GroupKind::AxisReduce) {
+        G.threads = 256;
         nl += 1;
       } else {
         choose_stencil_tiling(G);

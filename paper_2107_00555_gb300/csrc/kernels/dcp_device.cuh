@@ -227,6 +227,20 @@ template <typename T> struct DcpStParamsT {
   unsigned int* ticket;
 };
 
+// Launch parameters of axis-reduction kernels (passed by value).  The
+// iteration space is viewed as (outer, R, inner) with R the reduced axis.
+template <typename T> struct DcpAxParamsT {
+  const T* ld[DCP_MAXIO];   // prologue loads (full iteration space)
+  const T* sc[DCP_MAXIO];   // 0-axis operands
+  T* out[DCP_MAXIO];        // one output of outer * inner elements per reduction
+  typename DcpFin<T>::type* partials;  // [NRED][S][outer * inner] when S > 1
+  unsigned int* tickets;    // one per block tile (S > 1)
+  long long outer, R, inner;
+  long long rchunk;         // elements of R per split
+  long long ntiles;         // tiles of TI along inner
+  int TO, TI, TR, S;        // threads along outer / inner / R (powers of 2), R splits
+};
+
 template <typename T, int VEC> union DcpPack {
   uint4 u;
   T t[VEC];

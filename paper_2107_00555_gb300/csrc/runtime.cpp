@@ -43,6 +43,18 @@ struct StParamsH {
   void* partials;
   void* ticket;
 };
+struct AxParamsH {
+  const void* ld[kMaxIO];
+  const void* sc[kMaxIO];
+  void* out[kMaxIO];
+  void* partials;
+  void* tickets;
+  int64_t outer, R, inner;
+  int64_t rchunk;
+  int64_t ntiles;
+  int32_t TO, TI, TR, S;
+};
+static_assert(sizeof(AxParamsH) == 3 * kMaxIO * 8 + 16 + 40 + 16, "axis params layout");
 struct InstH {
   const void* in;
   void* out;
@@ -83,6 +95,8 @@ struct GroupRT {
   void* partials = nullptr;
   int partial_slots = 0;
   unsigned* ticket = nullptr;
+  unsigned* tickets = nullptr;   // axis reductions: one per block tile
+  int64_t ntickets = 0;
   std::vector<int64_t> offsets;  // batch: element offset of each member in a slab
   std::map<int, Table> tables;   // batch: per chunk
 };
@@ -148,6 +162,14 @@ GraphImpl::~GraphImpl() = default;
 static std::vector<LaunchSpec> build_group_launches(GraphImpl& g, int gi) {
   std::vector<LaunchSpec> L;
   const Group& G = g.groups[gi];
+  if (G.kind == GroupKind::AxisReduce) {
+    LaunchSpec ls;
+    ls.group = gi;
+    ls.code = gen_axis_kernel(g, G);
+    nvrtc_compile(ls.code.source, ls.code.name, &ls.compile_ms, nullptr);
+    L.push_back(std::move(ls));
+    return L;
+  }
   if (G.kind == GroupKind::Map) {
     LaunchSpec ls;
     ls.group = gi;
@@ -285,10 +307,91 @@ static void* group_partials(GraphImpl& g, int gi, int64_t slots) {
   return R.partials;
 }
 
+// Zeroed tickets of an axis-reduction group (cleared on the launch stream;
+// every launch leaves them zero again).
+static unsigned* group_tickets(GraphImpl& g, int gi, int64_t n, cudaStream_t s) {
+  auto& rt = *g.rt;
+  GroupRT& R = rt.grt[gi];
+  if (n < 1) n = 1;
+  if (!R.tickets || R.ntickets < n) {
+    R.tickets = (unsigned*)dalloc(rt, (size_t)n * sizeof(unsigned));
+    check_cuda(cudaMemsetAsync(R.tickets, 0, (size_t)n * sizeof(unsigned), s), "cudaMemsetAsync(tickets)");
+    R.ntickets = n;
+  }
+  return R.tickets;
+}
+
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int64_t pow2ceil(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Axis reduction: the (outer, R, inner) view of the iteration space, a
+// power-of-two thread layout along (outer, R, inner) that keeps consecutive
+// threads on the contiguous axis, and an R split when the tiles alone would
+// not fill the GPU.
+static void launch_axis(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
+                        cudaStream_t s) {
+  auto& rt = *g.rt;
+  const Group& G = g.groups[ls.group];
+  AxParamsH p;
+  std::memset(&p, 0, sizeof p);
+  const size_t esz = dtype_size(G.dtype);
+  for (size_t i = 0; i < G.loads.size(); ++i) {
+    p.ld[i] = ptr[G.loads[i]];
+    if ((uintptr_t)p.ld[i] % esz) fail(DCP_E_INVALID_ARG, "buffer not aligned to its element size");
+  }
+  for (size_t i = 0; i < G.scalars.size(); ++i) p.sc[i] = ptr[G.scalars[i]];
+  for (size_t i = 0; i < G.reds.size(); ++i) {
+    p.out[i] = const_cast<void*>(ptr[G.reds[i]]);
+    if ((uintptr_t)p.out[i] % esz) fail(DCP_E_INVALID_ARG, "buffer not aligned to its element size");
+  }
+  int64_t outer = 1, inner = 1;
+  for (int d = 0; d < G.axis; ++d) outer *= G.shape[d];
+  for (int d = G.axis + 1; d < (int)G.shape.size(); ++d) inner *= G.shape[d];
+  const int64_t R = G.shape[G.axis];
+  if (outer * inner == 0) return;
+  const int threads = ls.code.threads;
+  const int64_t TI = std::min<int64_t>(pow2ceil(inner), threads);
+  // rows of up to 4096 contiguous elements: at most a warp per row (shuffle
+  // tree, several rows per CTA); otherwise as many threads as fit
+  const int64_t trmax = (inner == 1 && R <= 4096) ? 32 : threads / TI;
+  const int64_t TR = std::min<int64_t>(pow2ceil(std::max<int64_t>(R, 1)), trmax);
+  const int64_t TO = threads / (TI * TR);
+  const int64_t ntiles = (inner + TI - 1) / TI;
+  const int64_t base = (outer + TO - 1) / TO * ntiles;
+  const int64_t target = (int64_t)rt.sms * std::max(1, ls.occupancy);
+  int64_t S = 1;
+  if (base < target && R > TR * 32)
+    S = std::min<int64_t>({(target + base - 1) / base, (R + TR * 32 - 1) / (TR * 32), 65535});
+  int64_t rchunk = std::max<int64_t>(1, (R + S - 1) / S);
+  S = std::max<int64_t>(1, (R + rchunk - 1) / rchunk);
+  const int64_t grid = base;  // one CTA per tile (and per split of R)
+  if (grid > 0x7fffffff) fail(DCP_E_SHAPE, "axis reduction grid too large");
+  p.outer = outer;
+  p.R = R;
+  p.inner = inner;
+  p.rchunk = S == 1 ? std::max<int64_t>(R, 1) : rchunk;
+  p.ntiles = ntiles;
+  p.TO = (int32_t)TO;
+  p.TI = (int32_t)TI;
+  p.TR = (int32_t)TR;
+  p.S = (int32_t)S;
+  if (S > 1) {
+    p.partials = group_partials(g, ls.group, S * outer * inner);
+    p.tickets = group_tickets(g, ls.group, base, s);
+  }
+  void* args[] = {&p};
+  check_cu(drv().launchKernel(ls.fn, (unsigned)grid, (unsigned)S, 1, threads, 1, 1, 0, (CUstream)s,
+                              args, nullptr),
+           "cuLaunchKernel(axis reduction)");
+}
 
 static void launch_map(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
                        cudaStream_t s) {
@@ -485,6 +588,7 @@ static void launch_one(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
                        cudaStream_t s) {
   const Group& G = g.groups[ls.group];
   if (G.kind == GroupKind::Map) launch_map(g, ls, ptr, s);
+  else if (G.kind == GroupKind::AxisReduce) launch_axis(g, ls, ptr, s);
   else if (G.kind == GroupKind::Stencil) launch_stencil(g, ls, ptr, s);
   else launch_batch(g, ls, ptr, s);
 }
@@ -507,7 +611,7 @@ static std::vector<const void*> bind(GraphImpl& g, const void* const* inputs,
   }
   for (size_t j = 0; j < g.outputs.size(); ++j) {
     const Node& n = g.nodes[g.outputs[j]];
-    if (!outputs[j] && (n.numel() > 0 || n.kind == Kind::Reduce))
+    if (!outputs[j] && (n.numel() > 0 || (n.kind == Kind::Reduce && n.axis < 0)))
       fail(DCP_E_INVALID_ARG, "output " + std::to_string(j) + " is NULL");
     ptr[g.outputs[j]] = outputs[j];
   }
@@ -656,7 +760,7 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
   check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
   for (int gi = 0; gi < (int)g.groups.size(); ++gi) {
     const Group& G = g.groups[gi];
-    if (G.kind == GroupKind::Map) {
+    if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce) {
       launch_group(g, gi, ptr, s);
       continue;
     }
@@ -831,7 +935,11 @@ std::string describe_plan(const GraphImpl& g) {
   for (size_t gi = 0; gi < g.groups.size(); ++gi) {
     const Group& G = g.groups[gi];
     if (gi) os << ", ";
-    const char* kind = G.kind == GroupKind::Map ? "map" : (G.kind == GroupKind::Stencil ? "stencil" : "batch");
+    const char* kind = G.kind == GroupKind::Map
+                           ? "map"
+                           : (G.kind == GroupKind::Stencil
+                                  ? "stencil"
+                                  : (G.kind == GroupKind::AxisReduce ? "axis_reduce" : "batch"));
     os << "{\"kind\": \"" << kind << "\", \"dtype\": \"" << dtype_name(G.dtype) << "\", \"shape\": [";
     for (size_t i = 0; i < G.shape.size(); ++i) os << (i ? ", " : "") << G.shape[i];
     os << "], \"members\": " << G.members.size() << ", \"post\": " << G.post.size()
@@ -840,7 +948,8 @@ std::string describe_plan(const GraphImpl& g) {
        << ", \"steps\": " << G.steps.size() << ", \"depth\": " << G.depth << ", \"tile\": ["
        << G.tile[0] << ", " << G.tile[1] << ", " << G.tile[2] << "]";
     if (G.kind == GroupKind::Batch) os << ", \"instances\": " << G.batch_members.size();
-    if (G.kind != GroupKind::Map)
+    if (G.kind == GroupKind::AxisReduce) os << ", \"axis\": " << G.axis;
+    if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce)
       os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
          << ", \"prefetch\": " << G.prefetch;
     int epi = 0;

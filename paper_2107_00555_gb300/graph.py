@@ -70,10 +70,18 @@ class Graph:
         self.dtype[out] = self.dtype[v]
         return out
 
-    def reduce(self, v, red="sum"):
+    def reduce(self, v, red="sum", axis=None):
+        """Reduction of all elements (axis=None) or along one axis (NumPy's
+        ``x.sum(axis=axis)``; negative axes count from the end)."""
         code = REDS[red] if isinstance(red, str) else int(red)
-        out = C.dcp_add_reduce(self._h, v, code)
-        self.shape[out] = ()
+        if axis is None:
+            out = C.dcp_add_reduce(self._h, v, code)
+            self.shape[out] = ()
+        else:
+            out = C.dcp_add_reduce_axis(self._h, v, code, int(axis))
+            shp = self.shape[v]
+            ax = int(axis) + len(shp) if int(axis) < 0 else int(axis)
+            self.shape[out] = tuple(s for d, s in enumerate(shp) if d != ax)
         self.dtype[out] = self.dtype[v]
         return out
 

@@ -202,3 +202,79 @@ def test_plan_3d_tile_options():
     g.fuse(C.DCP_FUSE_ALL)
     (grp,) = [x for x in g.plan()["groups"] if x["kind"] == "stencil"]
     assert grp["tile"] == [16, 4, 64]
+
+
+def test_axis_reduce_shapes_and_errors():
+    g = Graph()
+    x = g.input("f32", (3, 4, 5))
+    assert g.shape[g.reduce(x, "sum", axis=1)] == (3, 5)
+    assert g.shape[g.reduce(x, "max", axis=-1)] == (3, 4)
+    with pytest.raises(DcpError) as e:
+        g.reduce(x, "sum", axis=3)
+    assert e.value.status == C.DCP_E_INVALID_ARG
+    s = g.reduce(x, "sum")
+    with pytest.raises(DcpError) as e:
+        g.reduce(s, "sum", axis=0)
+    assert e.value.status == C.DCP_E_SHAPE
+    z = g.input("f32", (0, 4))
+    with pytest.raises(DcpError) as e:
+        g.reduce(z, "max", axis=0)
+    assert e.value.status == C.DCP_E_SHAPE
+    g.reduce(z, "sum", axis=0)
+
+
+def test_plan_axis_reduce_fusion():
+    g = Graph()
+    x = g.input("f64", (8, 9))
+    y = g.map("square", [x])
+    g.output(g.reduce(y, "sum", axis=0))
+    g.output(g.reduce(y, "max", axis=0))
+    g.output(g.reduce(x, "min", axis=1))
+    assert g.fuse(C.DCP_FUSE_ALL) == 2
+    k = [(gr["kind"], gr["axis"], gr["members"], gr["reductions"]) for gr in g.plan()["groups"]]
+    assert k == [("axis_reduce", 0, 1, 2), ("axis_reduce", 1, 0, 1)]
+    # a value also needed elsewhere stays a map group of its own
+    g = Graph()
+    x = g.input("f64", (8, 9))
+    y = g.map("square", [x])
+    g.output(y)
+    g.output(g.reduce(y, "sum", axis=1))
+    assert g.fuse(C.DCP_FUSE_ALL) == 2
+    assert [gr["kind"] for gr in g.plan()["groups"]] == ["map", "axis_reduce"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "i64"])
+def test_every_kernel_family_compiles(dtype):
+    """dcp_fuse generates and NVRTC-compiles (for sm_103a, no GPU needed)
+    every kernel family the dtype supports: fused maps with full and axis
+    reductions, and for floating types 1-D / 2-D / 3-D stencils under every
+    boundary rule and kernel form, batches and the reverse-pass maps."""
+    g = Graph()
+    x = g.input(dtype, (6, 7, 8))
+    y = g.map("add", [g.map("mul", [x, x]), x])
+    g.output(g.reduce(y, "sum"))
+    g.output(g.reduce(y, "max", axis=0))
+    g.output(g.reduce(y, "min", axis=1))
+    g.output(g.reduce(y, "maxabs", axis=2))
+    g.output(g.reduce(x, "sum", axis=-1))
+    g.fuse(C.DCP_FUSE_ALL)
+    g0 = Graph()
+    x0 = g0.input(dtype, (6, 7))
+    g0.output(g0.reduce(g0.map("neg", [x0]), "sum", axis=1))
+    g0.fuse(0)
+    if dtype.startswith("i"):
+        return
+    for bc in ("zero", "periodic", "fixed_ring"):
+        for kernel in (0, 1):
+            for shape, offs in (((40,), [(-1,), (0,), (1,)]),
+                                ((20, 30), [(0, 0), (0, -1), (0, 1), (1, 0), (-1, 0)]),
+                                ((20, 30), [(0, 0), (0, -2), (0, 2), (2, 0), (-2, 0)])):
+                g = Graph()
+                v = g.input(dtype, shape)
+                s = g.map("tanh", [g.stencil(g.map("abs", [v]), offs, [0.2] * len(offs), bc, 3)])
+                g.output(g.reduce(g.stencil(s, offs, [0.2] * len(offs), bc, 2), "sum"))
+                g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+                g.fuse(C.DCP_FUSE_ALL)
+        programs.heat3d((9, 10, 11), 2, bc, dtype, fuse=C.DCP_FUSE_ALL)
+    programs.batch2d([5, 40, 70], 6, "zero", dtype, fuse=C.DCP_FUSE_ALL | C.DCP_BATCH)
+    programs.tanh_chain((8, 9, 10), 2, "periodic", dtype, fuse=C.DCP_FUSE_ALL)

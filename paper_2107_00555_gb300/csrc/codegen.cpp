@@ -185,33 +185,43 @@ CodegenOut gen_map_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
 
 // Axis reduction (k_axis.cuh): the reduced operands, with the fused
 // prologue maps, at a flat index of the iteration space.
-CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& G) {
+CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
   NameScope names;
   std::ostringstream os;
   const int T = G.dtype;
+  int64_t inner = 1;
+  for (int d = G.axis + 1; d < (int)G.shape.size(); ++d) inner *= G.shape[d];
+  const int64_t R = G.shape[G.axis];
+  // 16-byte vectors along the contiguous axis when the shape allows it and
+  // the reduction tree's shared memory stays within 32 KB
+  const int axmode = inner > 1 ? 0 : 1;
+  int vec = vec_ok ? 16 / dtype_size(T) : 1;
+  if ((axmode == 0 ? inner : R) % vec != 0 || (int)G.reds.size() * vec > 16) vec = 1;
   os << "// dcp axis reduction kernel: " << G.members.size() << " prologue ops, " << G.loads.size()
      << " loads, " << G.reds.size() << " reductions along axis " << G.axis << "\n";
   os << "#define DCP_T " << dtype_cname(T) << "\n#define DCP_THREADS " << G.threads
-     << "\n#define DCP_NRED " << G.reds.size() << "\n#define DCP_NSCALAR " << G.scalars.size()
-     << "\n";
+     << "\n#define DCP_NRED " << G.reds.size() << "\n#define DCP_NLOAD " << G.loads.size()
+     << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n#define DCP_VEC " << vec
+     << "\n#define DCP_AXMODE " << axmode << "\n";
   os << red_op_fn(g, G.reds);
   os << "#include \"dcp_device.cuh\"\n";
-  os << "__device__ __forceinline__ void dcp_elem(const DcpAxParamsT<DCP_T>& p, const DCP_T* sc, "
-        "long long gi, DCP_T* rv) {\n";
+  os << "__device__ __forceinline__ void dcp_body(const DCP_T* ld, const DCP_T* sc, DCP_T* rv) {\n";
   for (size_t i = 0; i < G.loads.size(); ++i)
-    os << "  const DCP_T " << var(G.loads[i]) << " = p.ld[" << i << "][gi];\n";
+    os << "  const DCP_T " << var(G.loads[i]) << " = ld[" << i << "];\n";
   for (size_t i = 0; i < G.scalars.size(); ++i)
     os << "  const DCP_T " << var(G.scalars[i]) << " = sc[" << i << "];\n";
   emit_members(os, g, G.members);
   for (size_t i = 0; i < G.reds.size(); ++i)
     os << "  rv[" << i << "] = " << var(g.nodes[G.reds[i]].in[0]) << ";\n";
-  os << "  (void)p; (void)sc; (void)gi;\n}\n";
+  os << "  (void)ld; (void)sc;\n}\n";
   os << "#include \"k_axis.cuh\"\n";
   CodegenOut out;
   out.source = finish("dcp_axis", os.str());
   out.name = kname_of(out.source);
   out.threads = G.threads;
   out.smem_bytes = 0;
+  out.vec = vec;
+  out.axmode = axmode;
   return out;
 }
 

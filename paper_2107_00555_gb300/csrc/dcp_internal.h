@@ -217,12 +217,14 @@ struct CodegenOut {
   std::string source;
   int smem_bytes = 0;
   int threads = 256;
+  int vec = 1;     // axis reductions: elements per load
+  int axmode = 0;  // axis reductions: 0 vectors along inner, 1 along the reduced axis
 };
 CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 // Stencil launch `chunk` covers steps [s0, s1) of the group.
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
 CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
-CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& grp);
+CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 // adjoint kernels
 CodegenOut gen_map_adjoint_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int step);

@@ -165,7 +165,8 @@ static std::vector<LaunchSpec> build_group_launches(GraphImpl& g, int gi) {
   if (G.kind == GroupKind::AxisReduce) {
     LaunchSpec ls;
     ls.group = gi;
-    ls.code = gen_axis_kernel(g, G);
+    ls.code = gen_axis_kernel(g, G, true);
+    ls.code_scalar = gen_axis_kernel(g, G, false);
     nvrtc_compile(ls.code.source, ls.code.name, &ls.compile_ms, nullptr);
     L.push_back(std::move(ls));
     return L;
@@ -343,8 +344,10 @@ static void launch_axis(GraphImpl& g, LaunchSpec& ls, const std::vector<const vo
   AxParamsH p;
   std::memset(&p, 0, sizeof p);
   const size_t esz = dtype_size(G.dtype);
+  bool vec = ls.code.vec > 1;
   for (size_t i = 0; i < G.loads.size(); ++i) {
     p.ld[i] = ptr[G.loads[i]];
+    vec = vec && aligned16(p.ld[i]);
     if ((uintptr_t)p.ld[i] % esz) fail(DCP_E_INVALID_ARG, "buffer not aligned to its element size");
   }
   for (size_t i = 0; i < G.scalars.size(); ++i) p.sc[i] = ptr[G.scalars[i]];
@@ -357,20 +360,49 @@ static void launch_axis(GraphImpl& g, LaunchSpec& ls, const std::vector<const vo
   for (int d = G.axis + 1; d < (int)G.shape.size(); ++d) inner *= G.shape[d];
   const int64_t R = G.shape[G.axis];
   if (outer * inner == 0) return;
+  CUfunction fn = ls.fn;
+  int occ = ls.occupancy;
+  if (!vec && ls.code.vec > 1) {
+    if (!ls.fn_scalar) {
+      ls.fn_scalar = load_function(ls.code_scalar.source, ls.code_scalar.name, nullptr, nullptr);
+      check_cu(drv().occupancy(&ls.occ_scalar, ls.fn_scalar, ls.code_scalar.threads, 0),
+               "occupancy query");
+    }
+    fn = ls.fn_scalar;
+    occ = ls.occ_scalar;
+  }
+  const int64_t V = vec ? ls.code.vec : 1;
+  const bool along_inner = ls.code.axmode == 0;
   const int threads = ls.code.threads;
-  const int64_t TI = std::min<int64_t>(pow2ceil(inner), threads);
+  const int64_t target = (int64_t)rt.sms * std::max(1, occ);
+  // threads along inner cover V adjacent indices each when vectors run along inner
+  int64_t TI = along_inner ? std::min<int64_t>(pow2ceil((inner + V - 1) / V), threads) : 1;
   // rows of up to 4096 contiguous elements: at most a warp per row (shuffle
   // tree, several rows per CTA); otherwise as many threads as fit
   const int64_t trmax = (inner == 1 && R <= 4096) ? 32 : threads / TI;
-  const int64_t TR = std::min<int64_t>(pow2ceil(std::max<int64_t>(R, 1)), trmax);
+  const int64_t rv = along_inner ? 1 : V;  // elements of R per thread and step
+  int64_t TR = std::min<int64_t>(pow2ceil(std::max<int64_t>((R + rv - 1) / rv, 1)), trmax);
+  auto tiles_of = [&](int64_t ti, int64_t tr) {
+    const int64_t to = threads / (ti * tr);
+    const int64_t span = ti * (along_inner ? V : 1);
+    return (outer + to - 1) / to * ((inner + span - 1) / span);
+  };
+  // fewer than about four waves of tiles: move threads from inner to R (down
+  // to a warp along inner, a 32*V-element contiguous span per load) while R
+  // has work for them; fewer splits of R follow
+  while (along_inner && TI > 32 && tiles_of(TI, TR) < 4 * target && R >= TR * 16) {
+    TI >>= 1;
+    TR <<= 1;
+  }
   const int64_t TO = threads / (TI * TR);
-  const int64_t ntiles = (inner + TI - 1) / TI;
+  const int64_t ntiles = (inner + TI * (along_inner ? V : 1) - 1) / (TI * (along_inner ? V : 1));
   const int64_t base = (outer + TO - 1) / TO * ntiles;
-  const int64_t target = (int64_t)rt.sms * std::max(1, ls.occupancy);
   int64_t S = 1;
-  if (base < target && R > TR * 32)
-    S = std::min<int64_t>({(target + base - 1) / base, (R + TR * 32 - 1) / (TR * 32), 65535});
+  if (base < target && R > TR * rv * 32)
+    S = std::min<int64_t>({(target + base - 1) / base, (R + TR * rv * 32 - 1) / (TR * rv * 32), 65535});
+  // splits start on a vector boundary of R
   int64_t rchunk = std::max<int64_t>(1, (R + S - 1) / S);
+  rchunk = (rchunk + rv - 1) / rv * rv;
   S = std::max<int64_t>(1, (R + rchunk - 1) / rchunk);
   const int64_t grid = base;  // one CTA per tile (and per split of R)
   if (grid > 0x7fffffff) fail(DCP_E_SHAPE, "axis reduction grid too large");
@@ -388,7 +420,7 @@ static void launch_axis(GraphImpl& g, LaunchSpec& ls, const std::vector<const vo
     p.tickets = group_tickets(g, ls.group, base, s);
   }
   void* args[] = {&p};
-  check_cu(drv().launchKernel(ls.fn, (unsigned)grid, (unsigned)S, 1, threads, 1, 1, 0, (CUstream)s,
+  check_cu(drv().launchKernel(fn, (unsigned)grid, (unsigned)S, 1, threads, 1, 1, 0, (CUstream)s,
                               args, nullptr),
            "cuLaunchKernel(axis reduction)");
 }

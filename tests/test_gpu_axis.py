@@ -21,7 +21,12 @@ NP = {"f32": np.float32, "f64": np.float64, "i32": np.int32, "i64": np.int64}
 SHAPES_AXES = [((1,), 0), ((5,), 0), ((37, 45), 0), ((37, 45), 1), ((3, 5, 7), 0),
                ((3, 5, 7), 1), ((3, 5, 7), 2), ((1000, 3), 0), ((1000, 3), 1),
                ((3, 100003), 1), ((100003, 3), 0), ((64, 4096), 1), ((4096, 64), 0),
-               ((2, 1, 5), 1), ((7, 300, 9), 1), ((1, 1 << 20), 1), ((1 << 20, 1), 0)]
+               ((2, 1, 5), 1), ((7, 300, 9), 1), ((1, 1 << 20), 1), ((1 << 20, 1), 0),
+               # extents divisible by the vector width: 16-byte loads along the
+               # contiguous axis (inner, or the reduced axis for contiguous rows)
+               ((36, 44), 0), ((36, 44), 1), ((8, 5, 12), 0), ((8, 5, 12), 1), ((8, 5, 12), 2),
+               ((4, 100000), 0), ((100000, 4), 1), ((3, 100004), 1), ((100004, 8), 0),
+               ((64, 8), 1), ((5, 4096), 1)]
 
 
 def _data(shape, dtype, seed):
@@ -154,3 +159,19 @@ def test_axis_reduction_op_by_op_and_errors():
     with pytest.raises(C.DcpError) as e:
         g.adjoint([to_dev(np.ones((3, 4)))], [to_dev(np.ones(3))])
     assert e.value.status == C.DCP_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3])
+@pytest.mark.parametrize("shape,axis", [((64, 400), 0), ((64, 400), 1)])
+def test_unaligned_buffers_take_the_scalar_variant(offset, shape, axis):
+    """Inputs that start off a 16-byte boundary use the element-wise loads."""
+    n = int(np.prod(shape))
+    x = _data((n + offset,), "f32", 13)
+    d = to_dev(x)[offset:].view(shape)
+    g = _graph(shape, "f32", axis, ["sum", "max"])
+    g.fuse(C.DCP_FUSE_ALL)
+    s, m = (to_host(o) for o in g.run([d]))
+    xs = x[offset:].reshape(shape)
+    _, fs, ab = oracle.reduce_axis("sum", xs, axis)
+    assert np.all(np.abs(s.astype(np.float64) - fs) <= 1e-4 * ab)
+    assert np.array_equal(m.astype(np.float64), oracle.reduce_axis("max", xs, axis))

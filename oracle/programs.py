@@ -11,13 +11,15 @@ W5 = [0.2] * 5
 W7 = [0.4] + [0.1] * 6
 
 
-def map_reduce(n, dtype="f64"):
-    """y = exp(a*x + b) * sin(x) - 0.5*x*x, then sum(y) and max|y|.
+def map_reduce(n, dtype="f64", axis=None):
+    """y = exp(a*x + b) * sin(x) - 0.5*x*x, then sum(y) and max|y| (``n`` an
+    element count or a shape; with ``axis``, along that axis).
     Handles: x, a, b, ax, t, e, s, p, xx, h, y, sum, maxabs."""
+    shape = (n,) if isinstance(n, int) else tuple(n)
     p = Program()
-    x = p.input(dtype, (n,))
-    a = p.input(dtype, (n,))
-    b = p.input(dtype, (n,))
+    x = p.input(dtype, shape)
+    a = p.input(dtype, shape)
+    b = p.input(dtype, shape)
     ax = p.map("mul", [a, x])
     t = p.map("add", [ax, b])
     e = p.map("exp", [t])
@@ -26,8 +28,8 @@ def map_reduce(n, dtype="f64"):
     xx = p.map("mul", [x, x])
     h = p.map("mul_s", [xx], 0.5)
     y = p.map("sub", [pr, h])
-    p.output(p.reduce(y, "sum"))
-    p.output(p.reduce(y, "maxabs"))
+    p.output(p.reduce(y, "sum", axis=axis))
+    p.output(p.reduce(y, "maxabs", axis=axis))
     p.handles = dict(x=x, a=a, b=b, p=pr, h=h, y=y)
     return p
 

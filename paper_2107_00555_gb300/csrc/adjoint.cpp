@@ -22,6 +22,8 @@
 #include <map>
 #include <set>
 
+#include <sstream>
+
 #include "dcp_internal.h"
 
 namespace dcp {
@@ -584,5 +586,29 @@ void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
 std::shared_ptr<AdjointState> new_adjoint_state() { return std::make_shared<AdjointState>(); }
 size_t adjoint_tape_bytes(const AdjointState& st) { return st.plan.tape_bytes; }
 bool adjoint_chunked(const AdjointState& st) { return st.plan.chunked; }
+
+// The reverse pass's kernels in execution order (JSON array).
+std::string adjoint_launches_json(const AdjointState& st) {
+  std::ostringstream os;
+  os << "[";
+  bool first = true;
+  auto add = [&](const Sub& x, const char* phase) {
+    if (!x.g) return;
+    for (const std::string& k : launch_kernel_names(*x.g)) {
+      os << (first ? "" : ", ") << "{\"phase\": \"" << phase << "\", \"kernel\": \"" << k
+         << "\"}";
+      first = false;
+    }
+  };
+  if (st.built) {
+    add(st.plan.forward, "forward");
+    for (size_t c = 0; c < st.plan.seg_rev.size(); ++c) {
+      if (st.plan.chunked) add(st.plan.seg_fwd[c], "recompute");
+      add(st.plan.seg_rev[c], "reverse");
+    }
+  }
+  os << "]";
+  return os.str();
+}
 
 }  // namespace dcp

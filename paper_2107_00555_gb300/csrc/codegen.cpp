@@ -125,19 +125,26 @@ std::string red_op_fn(const GraphImpl& g, const std::vector<int>& reds) {
   return os.str();
 }
 
-// Hash of the hand-written skeletons: part of every kernel name, so a name
-// (and the compiled-module caches keyed by the source) changes whenever the
-// skeleton it instantiates changes.
-uint64_t skeleton_hash() {
-  static const uint64_t h = fnv1a(std::string(device_header_source()) + kernel_map_source() +
-                                  kernel_stencil2d_source() + kernel_stencil3d_source() +
-                                  kernel_stream_source() + kernel_axis_source());
-  return h;
+// A kernel's name hashes its generated prefix together with the
+// hand-written skeletons it includes, so the name (and the compiled-module
+// caches keyed by the source) changes exactly when one of them changes.
+uint64_t skeleton_hash(const std::string& body) {
+  std::string text = device_header_source();
+  const std::pair<const char*, const char*> skel[] = {
+      {"k_map.cuh", kernel_map_source()},
+      {"k_stencil2d.cuh", kernel_stencil2d_source()},
+      {"k_stencil3d.cuh", kernel_stencil3d_source()},
+      {"k_stencil2d_stream.cuh", kernel_stream_source()},
+      {"k_axis.cuh", kernel_axis_source()}};
+  for (const auto& k : skel)
+    if (body.find(std::string("#include \"") + k.first + "\"") != std::string::npos) text += k.second;
+  return fnv1a(text);
 }
 
 std::string finish(const std::string& prefix, const std::string& body) {
   char name[64];
-  std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(), fnv1a(body) ^ skeleton_hash());
+  std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(),
+                fnv1a(body) ^ skeleton_hash(body));
   return std::string("#define DCP_KNAME ") + name + "\n" + body;
 }
 

@@ -209,6 +209,9 @@ void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
 std::shared_ptr<AdjointState> new_adjoint_state();
 size_t adjoint_tape_bytes(const AdjointState& st);
 bool adjoint_chunked(const AdjointState& st);
+std::string adjoint_launches_json(const AdjointState& st);
+// kernel names of a compiled graph's launches, in execution order
+std::vector<std::string> launch_kernel_names(const GraphImpl& g);
 std::string describe_plan(const GraphImpl& g);
 
 // codegen.cpp

@@ -1006,8 +1006,20 @@ std::string describe_plan(const GraphImpl& g) {
   for (size_t v = 0; v < g.nodes.size(); ++v)
     if (g.materialized.size() > v && g.materialized[v] && !is_io[v])
       tb += g.nodes[v].numel() * dtype_size(g.nodes[v].dtype);
-  os << tb << "}";
+  os << tb;
+  if (g.adj)
+    os << ", \"adjoint\": {\"tape_bytes\": " << adjoint_tape_bytes(*g.adj) << ", \"checkpointed\": "
+       << (adjoint_chunked(*g.adj) ? "true" : "false")
+       << ", \"launches\": " << adjoint_launches_json(*g.adj) << "}";
+  os << "}";
   return os.str();
+}
+
+std::vector<std::string> launch_kernel_names(const GraphImpl& g) {
+  std::vector<std::string> out;
+  if (g.rt)
+    for (const auto& ls : g.rt->launches) out.push_back(ls.code.name);
+  return out;
 }
 
 void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out_grads,

@@ -1,7 +1,8 @@
 """The workload programs, written against the dcp builder one NumPy-level
 operation per call (the SSA form of Sec. 2.3).
 
-* ``map_reduce``  y = exp(a*x + b) * sin(x) - 0.5*x*x; sum(y), max|y|
+* ``map_reduce``  y = exp(a*x + b) * sin(x) - 0.5*x*x; sum(y), max|y| (over
+                  all elements, or along one axis)
 * ``jacobi2d``    the 5-point averaging step of the paper's jacobi_2d
                   (Sec. 4.3), points in the order the paper sums them:
                   centre, west, east, south, north, all weighted 0.2
@@ -19,11 +20,14 @@ SEVEN_POINT = [(0, 0, 0), (0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 
 SEVEN_WEIGHTS = [0.4] + [0.1] * 6
 
 
-def map_reduce(n, dtype="f32", fuse=None):
+def map_reduce(n, dtype="f32", fuse=None, axis=None):
+    """``n`` is an element count (1-D arrays) or a shape; with ``axis`` the
+    two reductions run along that axis (one result per remaining index)."""
+    shape = (n,) if isinstance(n, int) else tuple(n)
     g = Graph()
-    x = g.input(dtype, (n,))
-    a = g.input(dtype, (n,))
-    b = g.input(dtype, (n,))
+    x = g.input(dtype, shape)
+    a = g.input(dtype, shape)
+    b = g.input(dtype, shape)
     t = g.map("mul", [a, x])
     t = g.map("add", [t, b])
     e = g.map("exp", [t])
@@ -32,8 +36,8 @@ def map_reduce(n, dtype="f32", fuse=None):
     xx = g.map("mul", [x, x])
     h = g.map("mul_s", [xx], 0.5)
     y = g.map("sub", [p, h])
-    g.output(g.reduce(y, "sum"))
-    g.output(g.reduce(y, "maxabs"))
+    g.output(g.reduce(y, "sum", axis=axis))
+    g.output(g.reduce(y, "maxabs", axis=axis))
     if fuse is not None:
         g.fuse(fuse)
     return g

@@ -126,3 +126,17 @@ def test_autograd_function_gradcheck():
     loss.backward()
     (ref,) = oracle.adjoint(OP.tanh_chain(shape, T), [u.detach().cpu().numpy()], [1.0])
     assert_close(u.grad.cpu().numpy(), ref, 1e-12, float(np.max(np.abs(ref))), "autograd")
+
+
+def test_plan_lists_the_reverse_pass_kernels():
+    shape, T = (12, 10, 14), 4
+    u0 = inputs.uniform(shape, -1.0, 1.0, 24)
+    g = programs.tanh_chain(shape, T, fuse=C.DCP_FUSE_ALL)
+    _adjoint(g, [u0], [np.array(1.0)])
+    adj = g.plan()["adjoint"]
+    phases = [l["phase"] for l in adj["launches"]]
+    assert phases[0] == "forward" and "reverse" in phases and not adj["checkpointed"]
+    assert adj["tape_bytes"] > 0
+    _adjoint(g, [u0], [np.array(1.0)], budget=5 * u0.nbytes)
+    adj = g.plan()["adjoint"]
+    assert adj["checkpointed"] and "recompute" in [l["phase"] for l in adj["launches"]]

@@ -129,7 +129,7 @@ def test_autograd_function_gradcheck():
 
 
 def test_plan_lists_the_reverse_pass_kernels():
-    shape, T = (12, 10, 14), 4
+    shape, T = (12, 10, 14), 9
     u0 = inputs.uniform(shape, -1.0, 1.0, 24)
     g = programs.tanh_chain(shape, T, fuse=C.DCP_FUSE_ALL)
     _adjoint(g, [u0], [np.array(1.0)])

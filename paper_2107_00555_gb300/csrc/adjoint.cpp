@@ -504,8 +504,9 @@ struct AdjointState {
 
 // Sub-programs are planned with the parent program's fusion flags, so the
 // reverse pass of an op-by-op program is op-by-op too.
-static void fuse_sub(Sub& s, uint32_t flags) {
+static void fuse_sub(Sub& s, uint32_t flags, const std::map<int, int64_t>& options) {
   if (!s.g) return;
+  s.g->options = options;  // the program's tiling and launch options apply to its reverse pass
   plan_graph(*s.g, flags & (DCP_FUSE_MAPS | DCP_FUSE_SUBGRAPH | DCP_TIME_TILE));
   compile_plan(*s.g);
   s.g->fused = true;
@@ -517,9 +518,9 @@ void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
   if (!st.built || st.budget != budget) {
     AdjointPlan p;
     plan_adjoint(g, budget, p);
-    fuse_sub(p.forward, g.flags);
-    for (Sub& x : p.seg_fwd) fuse_sub(x, g.flags);
-    for (Sub& x : p.seg_rev) fuse_sub(x, g.flags);
+    fuse_sub(p.forward, g.flags, g.options);
+    for (Sub& x : p.seg_fwd) fuse_sub(x, g.flags, g.options);
+    for (Sub& x : p.seg_rev) fuse_sub(x, g.flags, g.options);
     st.plan = std::move(p);
     st.budget = budget;
     st.built = true;

@@ -375,8 +375,13 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
   std::ostringstream os;
   os << "// dcp stencil kernel: " << nsteps << " steps per launch, bc " << G.bc << ", " << nd
      << "-D" << (batch ? ", batched" : "") << "\n";
+  // 3-D: paired cells along x when requested and the tile allows it; rows of
+  // the plane are then stored from an even offset so every pair is aligned
+  const int rz = G.radius[0], ry = G.radius[1], rx = G.radius[2];
+  const int CX3 = nd == 3 && G.cx == 2 && G.tile[2] % 2 == 0 && rx <= 2 ? 2 : 1;
+  const int threads = nd == 3 ? G.tile[2] * G.tile[1] / CX3 : G.threads;
   os << "#define DCP_T " << dtype_cname(T) << "\n";
-  os << "#define DCP_THREADS " << G.threads << "\n#define DCP_BC " << G.bc << "\n";
+  os << "#define DCP_THREADS " << threads << "\n#define DCP_BC " << G.bc << "\n";
   os << "#define DCP_LAST " << (last ? 1 : 0) << "\n#define DCP_BATCH " << (batch ? 1 : 0) << "\n";
   int nstore = last ? (int)G.stores.size() : 1;
   int nred = last ? (int)G.reds.size() : 0;
@@ -385,8 +390,7 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   CodegenOut out;
-  out.threads = G.threads;
-  const int rz = G.radius[0], ry = G.radius[1], rx = G.radius[2];
+  out.threads = threads;
   if (nd <= 2) {
     const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
     const int RY = nd == 1 ? 0 : ry;
@@ -418,22 +422,56 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
   } else {
     if (nsteps != 1) fail(DCP_E_UNSUPPORTED, "3-D stencil launches run one step each");
     const int TX = G.tile[2], TY = G.tile[1], TZ = G.tile[0];
-    const int PW = TX + 2 * rx, PH = TY + 2 * ry;
+    const int CX = CX3;
+    const int AX = CX == 2 ? (rx + 1) / 2 * 2 : rx;
+    const int PW = TX + 2 * AX, PH = TY + 2 * ry;
     os << "#define DCP_TX " << TX << "\n#define DCP_TY " << TY << "\n#define DCP_TZ " << TZ
        << "\n#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_RZ " << rz
-       << "\n";
+       << "\n#define DCP_CX " << CX << "\n#define DCP_AX " << AX << "\n";
     emit_stencil_io(os, g, G, first, last);
     const StepDesc& sd = G.steps[s0];
     const Node& sn = g.nodes[sd.node];
-    os << "__device__ __forceinline__ DCP_T dcp_sum3(const DCP_T* const* pl, int c) {\n";
-    for (int k = 0; k < sn.npts(); ++k) {
-      int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
-      std::string w = weight_literal(T, sn.weights[k]);
-      std::string x = "pl[" + std::to_string(dz + rz) + "][c + (" + std::to_string(dy * PW + dx) + ")]";
-      if (k == 0) os << "  DCP_T acc = dcp_mul_rn(" << w << ", " << x << ");\n";
-      else os << "  acc = dcp_fma_rn(" << w << ", " << x << ", acc);\n";
+    os << "__device__ __forceinline__ void dcp_sum3(const DCP_T* const* pl, int c, DCP_T (&v)["
+       << CX << "]) {\n";
+    if (CX == 1) {
+      for (int k = 0; k < sn.npts(); ++k) {
+        int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+        std::string w = weight_literal(T, sn.weights[k]);
+        std::string x = "pl[" + std::to_string(dz + rz) + "][c + (" + std::to_string(dy * PW + dx) + ")]";
+        if (k == 0) os << "  DCP_T acc = dcp_mul_rn(" << w << ", " << x << ");\n";
+        else os << "  acc = dcp_fma_rn(" << w << ", " << x << ", acc);\n";
+      }
+      os << "  v[0] = acc;\n";
+    } else {
+      // one aligned pair load per distinct (plane, pair index) the two cells read
+      auto floor_div2 = [](int o) { return o >= 0 ? o / 2 : -((-o + 1) / 2); };
+      std::map<std::pair<int, int>, std::string> pairs;
+      os << "  typedef typename DcpVec2<DCP_T>::type T2;\n";
+      for (int k = 0; k < sn.npts(); ++k)
+        for (int j = 0; j < 2; ++j) {
+          int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+          int q = floor_div2(dy * PW + dx + j);
+          auto key = std::make_pair(dz + rz, q);
+          if (pairs.count(key)) continue;
+          std::string nm = "p" + std::to_string(pairs.size());
+          pairs[key] = nm;
+          os << "  const T2 " << nm << " = *reinterpret_cast<const T2*>(pl[" << key.first
+             << "] + c + (" << 2 * q << "));\n";
+        }
+      for (int j = 0; j < 2; ++j) {
+        for (int k = 0; k < sn.npts(); ++k) {
+          int dz = G.offsets[k * 3], dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
+          int o = dy * PW + dx + j, q = floor_div2(o);
+          std::string x = pairs[std::make_pair(dz + rz, q)] + (o - 2 * q == 0 ? ".x" : ".y");
+          std::string w = weight_literal(T, sn.weights[k]);
+          std::string a = "a" + std::to_string(j);
+          if (k == 0) os << "  DCP_T " << a << " = dcp_mul_rn(" << w << ", " << x << ");\n";
+          else os << "  " << a << " = dcp_fma_rn(" << w << ", " << x << ", " << a << ");\n";
+        }
+        os << "  v[" << j << "] = a" << j << ";\n";
+      }
     }
-    os << "  return acc;\n}\n";
+    os << "}\n";
     os << "__device__ __forceinline__ DCP_T dcp_epi3(DCP_T v) {\n" << epi_body(g, sd) << "}\n";
     os << "#include \"k_stencil3d.cuh\"\n";
     out.smem_bytes = (2 * rz + 2) * PW * PH * dtype_size(T);

@@ -131,6 +131,7 @@ struct Group {
   int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
   int seg = 0;                  // warp stream: rows per work item (single arrays)
   int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
+  int cx = 1;                   // 3-D stencils: cells per thread along x (1 or 2)
   // axis-reduce groups: the reduced axis of the iteration space `shape`
   int axis = -1;
   // batch groups: the member stencil groups (same program, different shapes)

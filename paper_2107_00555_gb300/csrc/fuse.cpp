@@ -511,9 +511,13 @@ struct Planner {
     depth = std::max(1, std::min(depth, S));
     G.depth = depth;
     if (nd == 3) {
-      G.tile[0] = (int)opt(DCP_OPT_TILE_Z, 32);  // z chunk
+      G.tile[0] = (int)opt(DCP_OPT_TILE_Z, 16);  // z chunk
       G.tile[1] = (int)opt(DCP_OPT_TILE_Y, 8);
       G.tile[2] = (int)opt(DCP_OPT_TILE_X, 32);
+      // two cells per thread along x (two independent FP64 chains per
+      // thread, aligned pair loads) where the tile and radius allow it
+      const bool pairs_ok = G.tile[2] % 2 == 0 && G.radius[2] <= 2;
+      G.cx = pairs_ok ? (int)opt(DCP_OPT_CELLS_PER_THREAD, 2) : 1;
       G.threads = 256;
     } else {
       G.tile[0] = 1;

@@ -12,6 +12,11 @@ typedef unsigned long long dcp_u64;
 
 // Final-pass (cross-block) accumulator type: binary64 for floating groups
 // (an fp32 partial widens exactly), 64-bit integers for integer groups.
+// Aligned pair of elements (paired-cell stencil loads).
+template <typename T> struct DcpVec2;
+template <> struct DcpVec2<float> { typedef float2 type; };
+template <> struct DcpVec2<double> { typedef double2 type; };
+
 template <typename T> struct DcpFin { typedef double type; };
 template <> struct DcpFin<int> { typedef long long type; };
 template <> struct DcpFin<long long> { typedef long long type; };

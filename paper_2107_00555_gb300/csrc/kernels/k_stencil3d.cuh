@@ -10,11 +10,17 @@
 // maps, a prologue on the input and post maps / reductions on the output are
 // spliced in by the generator.
 //
+// With DCP_CX = 2 every thread computes two cells adjacent along x: rows of
+// the plane are stored from an even offset DCP_AX, so each pair of cells and
+// each pair of its neighbours is one aligned 2-element shared-memory load,
+// and the two weighted sums are independent chains of FP64 operations.
+//
 // The generated prefix defines DCP_T, DCP_TX, DCP_TY, DCP_TZ, DCP_RX,
-// DCP_RY, DCP_RZ, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST, DCP_NLOAD,
-// DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED, dcp_red_op(r) and
+// DCP_RY, DCP_RZ, DCP_CX, DCP_AX, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST,
+// DCP_NLOAD, DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)
-//   T    dcp_sum3(const T* const* pl, int c)   weighted sum; pl[dz + RZ] = plane z + dz
+//   void dcp_sum3(const T* const* pl, int c, T (&v)[DCP_CX])
+//        weighted sums of cells c .. c+CX-1 of the plane ring; pl[dz + RZ] = plane z + dz
 //   T    dcp_epi3(T v)                         epilogue maps fused after the step
 //   void dcp_post(const DcpStParams& p, const T* sc, long long i, T v, T* st, T* rv)
 typedef DCP_T T;
@@ -25,13 +31,18 @@ typedef typename DcpFin<T>::type F;
 #define DCP_BC_PERIODIC 1
 #define DCP_BC_FIXED_RING 2
 
-constexpr int DCP_PW = DCP_TX + 2 * DCP_RX;
+constexpr int DCP_LW = DCP_TX + 2 * DCP_RX;                   // loaded row: tile + halo
+constexpr int DCP_PW = DCP_TX + 2 * DCP_AX;                   // stored row (interior from DCP_AX)
 constexpr int DCP_PH = DCP_TY + 2 * DCP_RY;
-constexpr int DCP_PLANE = DCP_PW * DCP_PH;
-constexpr int DCP_NP = 2 * DCP_RZ + 1;                                     // planes read per output plane
-constexpr int DCP_NSLOT = DCP_NP + 1;                                      // ring slots
-constexpr int DCP_LPT = (DCP_PLANE + DCP_THREADS - 1) / DCP_THREADS;       // plane elements per thread
-constexpr int DCP_CPT = (DCP_TX * DCP_TY + DCP_THREADS - 1) / DCP_THREADS; // output cells per thread
+constexpr int DCP_PLANE = DCP_PW * DCP_PH;                    // stored plane
+constexpr int DCP_PLANE_LD = DCP_LW * DCP_PH;                 // loaded plane
+constexpr int DCP_NP = 2 * DCP_RZ + 1;                        // planes read per output plane
+constexpr int DCP_NSLOT = DCP_NP + 1;                         // ring slots
+constexpr int DCP_LPT = (DCP_PLANE_LD + DCP_THREADS - 1) / DCP_THREADS;  // plane elements per thread
+constexpr int DCP_UNITS = DCP_TX * DCP_TY / DCP_CX;           // cell groups per plane
+constexpr int DCP_CPT = (DCP_UNITS + DCP_THREADS - 1) / DCP_THREADS;   // cell groups per thread
+static_assert(DCP_CX == 1 || (DCP_TX % 2 == 0 && DCP_AX % 2 == 0 && DCP_AX >= DCP_RX),
+              "paired cells need an even row layout");
 
 typedef DcpStParamsT<T> DcpStParams;
 
@@ -60,7 +71,10 @@ __device__ __forceinline__ void dcp_store_plane(T* dst, const T (&v)[DCP_LPT]) {
 #pragma unroll
   for (int k = 0; k < DCP_LPT; ++k) {
     const int i = threadIdx.x + k * DCP_THREADS;
-    if (DCP_PLANE % DCP_THREADS == 0 || i < DCP_PLANE) dst[i] = v[k];
+    if (DCP_PLANE_LD % DCP_THREADS == 0 || i < DCP_PLANE_LD) {
+      const int ly = i / DCP_LW, lx = i - ly * DCP_LW;
+      dst[ly * DCP_PW + (DCP_AX - DCP_RX) + lx] = v[k];
+    }
   }
 }
 
@@ -85,9 +99,9 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #pragma unroll
   for (int k = 0; k < DCP_LPT; ++k) {
     const int i = threadIdx.x + k * DCP_THREADS;
-    const int ly = i / DCP_PW, lx = i - ly * DCP_PW;
+    const int ly = i / DCP_LW, lx = i - ly * DCP_LW;
     int y = y0 + ly, x = x0 + lx;
-    bool ok = i < DCP_PLANE;
+    bool ok = i < DCP_PLANE_LD;
     if (DCP_BC == DCP_BC_PERIODIC) {
       y = dcp_wrap(y, ny);
       x = dcp_wrap(x, nx);
@@ -116,31 +130,36 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #pragma unroll
     for (int k = 0; k < DCP_CPT; ++k) {
       const int i = threadIdx.x + k * DCP_THREADS;
-      if ((DCP_TX * DCP_TY) % DCP_THREADS != 0 && i >= DCP_TX * DCP_TY) break;
-      const int ty = i / DCP_TX, tx = i - ty * DCP_TX;
+      if (DCP_UNITS % DCP_THREADS != 0 && i >= DCP_UNITS) break;
+      const int ty = i / (DCP_TX / DCP_CX), tx = (i - ty * (DCP_TX / DCP_CX)) * DCP_CX;
       const int gy = tyi * DCP_TY + ty, gx = txi * DCP_TX + tx;
       if (gy >= ny || gx >= nx) continue;
-      const int c = (ty + DCP_RY) * DCP_PW + tx + DCP_RX;
-      T v;
-      if (DCP_BC == DCP_BC_FIXED_RING &&
-          (z < DCP_RZ || z >= nz - DCP_RZ || gy < DCP_RY || gy >= ny - DCP_RY || gx < DCP_RX ||
-           gx >= nx - DCP_RX)) {
-        v = dcp_epi3(pl[DCP_RZ][c]);  // ring cell keeps its value; epilogue still applies
-      } else {
-        v = dcp_epi3(dcp_sum3(pl, c));
-      }
-      const long long gi = ((long long)z * ny + gy) * nx + gx;
+      const int c = (ty + DCP_RY) * DCP_PW + tx + DCP_AX;
+      T v[DCP_CX];
+      dcp_sum3(pl, c, v);
+#pragma unroll
+      for (int j = 0; j < DCP_CX; ++j) {
+        if (j > 0 && gx + j >= nx) break;
+        if (DCP_BC == DCP_BC_FIXED_RING &&
+            (z < DCP_RZ || z >= nz - DCP_RZ || gy < DCP_RY || gy >= ny - DCP_RY ||
+             gx + j < DCP_RX || gx + j >= nx - DCP_RX)) {
+          v[j] = dcp_epi3(pl[DCP_RZ][c + j]);  // ring cell keeps its value; epilogue still applies
+        } else {
+          v[j] = dcp_epi3(v[j]);
+        }
+        const long long gi = ((long long)z * ny + gy) * nx + gx + j;
 #if DCP_LAST
-      T st[DCP_ARR(DCP_NSTORE)], rv[DCP_ARR(DCP_NRED)];
-      dcp_post(p, sc, gi, v, st, rv);
+        T st[DCP_ARR(DCP_NSTORE)], rv[DCP_ARR(DCP_NRED)];
+        dcp_post(p, sc, gi, v[j], st, rv);
 #pragma unroll
-      for (int s = 0; s < DCP_NSTORE; ++s) p.st[s][gi] = st[s];
+        for (int s = 0; s < DCP_NSTORE; ++s) p.st[s][gi] = st[s];
 #pragma unroll
-      for (int r = 0; r < DCP_NRED; ++r)
-        acc[r] = dcp_red_comb(dcp_red_op(r), acc[r], dcp_red_lift(dcp_red_op(r), rv[r]));
+        for (int r = 0; r < DCP_NRED; ++r)
+          acc[r] = dcp_red_comb(dcp_red_op(r), acc[r], dcp_red_lift(dcp_red_op(r), rv[r]));
 #else
-      p.st[0][gi] = v;
+        p.st[0][gi] = v[j];
 #endif
+      }
     }
   }
 #if DCP_LAST && DCP_NRED > 0

@@ -663,8 +663,12 @@ static void launch_all(GraphImpl& g, const std::vector<const void*>& ptr, cudaSt
 // in memory and, if DCP_TUNE_CACHE names a file, on disk.
 // ---------------------------------------------------------------------------
 namespace {
+// A tuned configuration: depth, tz, ty, tx, and for 3-D stencils the cells
+// per thread along x (stream kernels: tz = -1, ty = rows per item, tx =
+// prefetch depth).
+typedef std::array<int, 5> TuneCfg;
 std::mutex g_tune_mu;
-std::map<std::string, std::array<int, 4>> g_tune_cache;  // signature -> depth, tz, ty, tx
+std::map<std::string, TuneCfg> g_tune_cache;  // signature -> configuration
 bool g_tune_loaded = false;
 
 void tune_cache_load() {
@@ -673,17 +677,23 @@ void tune_cache_load() {
   const char* f = std::getenv("DCP_TUNE_CACHE");
   if (!f || !*f) return;
   std::ifstream in(f);
-  std::string key;
-  int d, z, y, x;
-  while (in >> key >> d >> z >> y >> x) g_tune_cache[key] = {d, z, y, x};
+  std::string line;
+  while (std::getline(in, line)) {
+    std::istringstream ls(line);
+    std::string key;
+    TuneCfg c = {1, 1, 1, 1, 1};
+    if (!(ls >> key >> c[0] >> c[1] >> c[2] >> c[3])) continue;
+    if (!(ls >> c[4])) c[4] = 1;  // entries without the fifth field
+    g_tune_cache[key] = c;
+  }
 }
 
-void tune_cache_store(const std::string& key, const std::array<int, 4>& v) {
+void tune_cache_store(const std::string& key, const TuneCfg& v) {
   g_tune_cache[key] = v;
   const char* f = std::getenv("DCP_TUNE_CACHE");
   if (!f || !*f) return;
   std::ofstream out(f, std::ios::app);
-  out << key << " " << v[0] << " " << v[1] << " " << v[2] << " " << v[3] << "\n";
+  out << key << " " << v[0] << " " << v[1] << " " << v[2] << " " << v[3] << " " << v[4] << "\n";
 }
 
 std::string group_signature(const GraphImpl& g, const Group& G, int device_sms) {
@@ -705,14 +715,19 @@ std::string group_signature(const GraphImpl& g, const Group& G, int device_sms) 
   return h;
 }
 
-std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
-  std::vector<std::array<int, 4>> c;
+std::vector<TuneCfg> tune_candidates(const Group& G) {
+  std::vector<TuneCfg> c;
   const int S = (int)G.steps.size();
   const int nd = group_nd(G);
   if (nd == 3) {
+    // one cell per thread (256-thread tiles) and paired cells along x
     const std::array<int, 3> tiles[] = {{32, 8, 32}, {64, 8, 32}, {16, 8, 32},
                                         {32, 4, 64}, {32, 16, 32}, {64, 4, 64}};
-    for (const auto& t : tiles) c.push_back({1, t[0], t[1], t[2]});
+    for (const auto& t : tiles) c.push_back({1, t[0], t[1], t[2], 1});
+    const std::array<int, 3> pair_tiles[] = {{16, 8, 32}, {32, 8, 32}, {16, 16, 32},
+                                             {32, 16, 32}, {16, 8, 64}, {32, 4, 64}};
+    if (G.radius[2] <= 2)
+      for (const auto& t : pair_tiles) c.push_back({1, t[0], t[1], t[2], 2});
     return c;
   }
   std::vector<int> depths;
@@ -726,7 +741,7 @@ std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
     for (const auto& t : tiles) {
       int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
       long smem = 2L * (t[0] + 2 * d * ry) * (t[1] + 2 * d * rx) * dtype_size(G.dtype);
-      if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1]});
+      if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1], 1});
     }
   // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item,
   // 0 = planner's; tx slot = row windows requested ahead)
@@ -734,20 +749,21 @@ std::vector<std::array<int, 4>> tune_candidates(const Group& G) {
     if (d <= S && stream_eligible(G, d))
       for (int pf : {1, 2}) {
         if (G.kind == GroupKind::Batch)
-          for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf});
+          for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf, 1});
         else
-          c.push_back({d, -1, 0, pf});
+          c.push_back({d, -1, 0, pf, 1});
       }
   return c;
 }
 
-void apply_config(GraphImpl& g, int gi, const std::array<int, 4>& cfg) {
+void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
   Group& G = g.groups[gi];
   G.depth = cfg[0];
   G.variant = cfg[1] < 0 ? 1 : 0;
   G.tile[0] = cfg[1] < 0 ? 1 : cfg[1];
   G.tile[1] = cfg[2];
   G.tile[2] = cfg[3];
+  G.cx = cfg[4] == 2 && G.tile[2] % 2 == 0 && G.radius[2] <= 2 ? 2 : 1;
   if (G.variant == 1) {
     auto th = g.options.find(DCP_OPT_STREAM_THREADS);
     G.threads = th == g.options.end() ? 64 : (int)th->second;
@@ -803,9 +819,8 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
       launch_group(g, gi, ptr, s);
       continue;
     }
-    std::array<int, 4> best = {G.depth, G.variant == 1 ? -1 : G.tile[0],
-                               G.variant == 1 ? G.seg : G.tile[1],
-                               G.variant == 1 ? G.prefetch : G.tile[2]};
+    TuneCfg best = {G.depth, G.variant == 1 ? -1 : G.tile[0], G.variant == 1 ? G.seg : G.tile[1],
+                    G.variant == 1 ? G.prefetch : G.tile[2], G.cx};
     float best_ms = 1e30f;
     for (const auto& cfg : tune_candidates(G)) {
       try {
@@ -981,6 +996,7 @@ std::string describe_plan(const GraphImpl& g) {
        << G.tile[0] << ", " << G.tile[1] << ", " << G.tile[2] << "]";
     if (G.kind == GroupKind::Batch) os << ", \"instances\": " << G.batch_members.size();
     if (G.kind == GroupKind::AxisReduce) os << ", \"axis\": " << G.axis;
+    if (G.kind == GroupKind::Stencil && G.shape.size() == 3) os << ", \"cells_per_thread\": " << G.cx;
     if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce)
       os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
          << ", \"prefetch\": " << G.prefetch;

@@ -80,6 +80,8 @@ def test_unknown_fuse_flag_and_options():
     assert _err(g.set_option, C.DCP_OPT_TILE_Z, 0) == C.DCP_E_INVALID_ARG
     assert _err(g.set_option, C.DCP_OPT_TILE_Z, 1025) == C.DCP_E_INVALID_ARG
     g.set_option(C.DCP_OPT_TILE_Z, 16)
+    assert _err(g.set_option, C.DCP_OPT_CELLS_PER_THREAD, 3) == C.DCP_E_INVALID_ARG
+    g.set_option(C.DCP_OPT_CELLS_PER_THREAD, 2)
     g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 3)
     g.fuse(0)
     assert _err(g.set_option, C.DCP_OPT_TIME_TILE_DEPTH, 2) == C.DCP_E_STATE
@@ -276,5 +278,8 @@ def test_every_kernel_family_compiles(dtype):
                 g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
                 g.fuse(C.DCP_FUSE_ALL)
         programs.heat3d((9, 10, 11), 2, bc, dtype, fuse=C.DCP_FUSE_ALL)
+        g = programs.heat3d((9, 10, 11), 2, bc, dtype)
+        g.set_option(C.DCP_OPT_CELLS_PER_THREAD, 2)
+        g.fuse(C.DCP_FUSE_ALL)
     programs.batch2d([5, 40, 70], 6, "zero", dtype, fuse=C.DCP_FUSE_ALL | C.DCP_BATCH)
     programs.tanh_chain((8, 9, 10), 2, "periodic", dtype, fuse=C.DCP_FUSE_ALL)

@@ -229,3 +229,58 @@ def test_stream_kernel_options_bitwise(shape, bc, dtype):
             continue  # too narrow a strip for this depth: tile kernel chosen
         got = to_host(g.run([to_dev(u0)])[0])
         assert got.tobytes() == base.tobytes(), (depth, pf, th, rows)
+
+
+@pytest.mark.parametrize("bc", ["zero", "periodic", "fixed_ring"])
+@pytest.mark.parametrize("shape", [(17, 19, 40), (40, 33, 71), (5, 9, 2)])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_heat3d_paired_cells_bitwise(bc, shape, dtype):
+    """Two cells per thread along x give the bits of one cell per thread."""
+    u0 = inputs.uniform(shape, -1.0, 1.0, 17, NP[dtype])
+    res = []
+    for cx, tile in ((1, None), (2, None), (2, (4, 16, 32)), (2, (8, 4, 64))):
+        g = programs.heat3d(shape, 3, bc, dtype)
+        g.set_option(C.DCP_OPT_CELLS_PER_THREAD, cx)
+        if tile is not None:
+            g.set_option(C.DCP_OPT_TILE_Z, tile[0])
+            g.set_option(C.DCP_OPT_TILE_Y, tile[1])
+            g.set_option(C.DCP_OPT_TILE_X, tile[2])
+        g.fuse(FUSED)
+        assert g.plan()["groups"][0]["cells_per_thread"] == cx
+        res.append(to_host(g.run([to_dev(u0)])[0]).tobytes())
+    assert all(r == res[0] for r in res)
+
+
+def test_radius2_3d_stencil_paired_cells():
+    shape = (12, 14, 37)
+    offs = [(0, 0, 0), (0, 0, -2), (0, 0, 2), (0, -2, 0), (0, 2, 0), (-2, 0, 0), (2, 0, 0),
+            (0, 0, -1), (0, 1, 1)]
+    w = [0.3, 0.1, 0.1, 0.1, 0.1, 0.1, 0.1, 0.05, 0.05]
+    u0 = inputs.uniform(shape, -1.0, 1.0, 18)
+    p = oracle.Program()
+    v = p.input("f64", shape)
+    p.output(p.stencil(v, offs, w, "zero", 2))
+    ref = oracle.run(p, [u0])[-1]
+    for cx in (1, 2):
+        g = Graph()
+        x = g.input("f64", shape)
+        g.output(g.stencil(x, offs, w, "zero", 2))
+        g.set_option(C.DCP_OPT_CELLS_PER_THREAD, cx)
+        g.fuse(FUSED)
+        assert_close(to_host(g.run([to_dev(u0)])[0]), ref, 1e-12, 1.0, "radius-2 3-D cx=%d" % cx)
+
+
+def test_tanh_chain_paired_cells_loss():
+    shape, T = (33, 20, 50), 3
+    u0 = inputs.uniform(shape, -1.0, 1.0, 19)
+    out = []
+    for cx in (1, 2):
+        g = programs.tanh_chain(shape, T)
+        g.set_option(C.DCP_OPT_CELLS_PER_THREAD, cx)
+        g.fuse(FUSED)
+        out.append(float(to_host(g.run([to_dev(u0)])[0])))
+    prog = OP.tanh_chain(shape, T)
+    vals, extra = oracle.run(prog, [u0], detail=True)
+    (lid,) = prog.outputs
+    for v in out:
+        assert abs(v - extra[lid]["fsum"]) <= 1e-10 * extra[lid]["abs"]

@@ -736,7 +736,7 @@ std::vector<TuneCfg> tune_candidates(const Group& G) {
   std::vector<std::array<int, 2>> tiles;
   if (nd == 1) tiles = {{1, 256}, {1, 512}, {1, 1024}};
   else if (G.dtype == DCP_F32) tiles = {{32, 64}, {64, 64}, {16, 128}, {32, 128}, {64, 32}};
-  else tiles = {{32, 32}, {16, 64}, {32, 64}, {64, 32}};
+  else tiles = {{32, 32}, {16, 64}, {32, 64}, {64, 32}, {16, 32}, {16, 16}, {8, 32}};
   for (int d : depths)
     for (const auto& t : tiles) {
       int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
@@ -748,10 +748,16 @@ std::vector<TuneCfg> tune_candidates(const Group& G) {
   for (int d : {1, 2, 3, 4, 5, 6, 8, 10})
     if (d <= S && stream_eligible(G, d))
       for (int pf : {1, 2}) {
-        if (G.kind == GroupKind::Batch)
+        if (G.kind == GroupKind::Batch) {
           for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf, 1});
-        else
+        } else {
           c.push_back({d, -1, 0, pf, 1});
+          // small arrays: short row segments spread the strips over more warps
+          const int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1;
+          if (ny <= 1024)
+            for (int seg : {8, 16, 32})
+              if (seg < ny) c.push_back({d, -1, seg, pf, 1});
+        }
       }
   return c;
 }
@@ -773,7 +779,9 @@ void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
     } else {
       int64_t ny = G.shape.size() == 2 ? G.shape[0] : 1, nx = G.shape.back();
       int64_t strips = (nx + stream_width(G) - 1) / stream_width(G);
-      int64_t seg = std::max<int64_t>((ny * strips + 2431) / 2432, 8 * G.depth * std::max(1, G.radius[1]));
+      int64_t seg = cfg[2] > 0 ? cfg[2]
+                               : std::max<int64_t>((ny * strips + 2431) / 2432,
+                                                   8 * G.depth * std::max(1, G.radius[1]));
       G.seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), std::max<int64_t>(ny, 1));
     }
   } else {

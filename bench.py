@@ -478,10 +478,21 @@ class Batch(Workload):
                 ("op_by_op", self.call0, self.g0.n_kernels)]
 
     def setup_e2e(self, torch):
-        self.h2d = self.d2h = None
+        # every instance in page-locked host memory, read and written there
+        # directly by the batched launches through dcp_run_host
+        self.pinned = []
+        for a in self.host:
+            t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+            t.copy_(torch.from_numpy(a))
+            self.pinned.append(t.numpy())
+        self.host_out = [torch.empty(a.shape, dtype=torch.float32, pin_memory=True).numpy()
+                         for a in self.host]
+        self.h2d = sum(a.nbytes for a in self.pinned)
+        self.d2h = sum(o.nbytes for o in self.host_out)
+        self.call_host = self.g.prepare_host(self.pinned, self.host_out)
 
     def step_e2e(self):
-        return None
+        self.call_host()
 
     def cpu_sample(self):
         import oracle
@@ -540,6 +551,20 @@ class Adjoint(Workload):
     def legs(self):
         return [("op_by_op", lambda: self.g0.adjoint(self.dev, self.ones, self.grad0), None)]
 
+    def setup_e2e(self, torch):
+        # u0 from page-locked host memory, the gradient back to it
+        self.torch = torch
+        self.u_host = torch.empty(self.shape, dtype=torch.float64, pin_memory=True)
+        self.u_host.copy_(torch.from_numpy(self.host[0]))
+        self.g_host = torch.empty(self.shape, dtype=torch.float64, pin_memory=True)
+        self.h2d = self.u_host.numel() * 8
+        self.d2h = self.g_host.numel() * 8
+
+    def step_e2e(self):
+        self.dev[0].copy_(self.u_host, non_blocking=True)
+        self.prog.adjoint(self.dev, self.ones, self.grad)
+        self.g_host.copy_(self.grad[0], non_blocking=True)
+
     def cpu_sample(self):
         import oracle
         from oracle import programs as OP
@@ -583,8 +608,8 @@ def _time_device(torch, fn, steps, stream):
     return start.elapsed_time(end) / 1e3
 
 
-def _per_launch(torch, fn, steps, stream):
-    """Average device duration of single launches (events around each)."""
+def _step_times(torch, fn, steps, stream):
+    """Device duration of each of `steps` single steps (events around each), s."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     torch.cuda.synchronize()
@@ -593,10 +618,32 @@ def _per_launch(torch, fn, steps, stream):
         fn()
         b.record(stream)
     torch.cuda.synchronize()
-    return statistics.mean(a.elapsed_time(b) for a, b in evs) / 1e3
+    return [a.elapsed_time(b) / 1e3 for a, b in evs]
+
+
+def median_ci95(xs):
+    """Median and a distribution-free 95 % confidence interval of the median
+    (order statistics of the binomial(n, 1/2) law, as the paper reports its
+    timings): returns (median, low, high)."""
+    from math import comb
+    v = sorted(xs)
+    n = len(v)
+    med = statistics.median(v)
+    # largest k with P(Binomial(n, 1/2) < k) <= 2.5 %: [v[k-1], v[n-k]] covers >= 95 %
+    k, cum = 0, 0.0
+    while k < n:
+        p = comb(n, k) / 2.0 ** n
+        if cum + p > 0.025:
+            break
+        cum += p
+        k += 1
+    if k == 0:
+        return med, v[0], v[-1]
+    return med, v[k - 1], v[n - k]
 
 
 FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (DFMA counted as 2 flops)
+HBM_NOMINAL_GBS = 8000.0   # nominal GB300 HBM3e bandwidth
 
 
 def reduce_max(value, dist=None, device=None):
@@ -623,7 +670,8 @@ def _roofline(wl, per_launch_s):
         achieved = work / per_launch_s / GB
         return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(wl.kernels[0]),
-                "kernel": wl.kernels[0], "peak_source": src}
+                "kernel": wl.kernels[0], "peak_source": src,
+                "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4)}
     achieved = work / per_launch_s / 1e9
     return {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
             "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
@@ -676,13 +724,16 @@ def run_dcp(args):
     t_step = t / args.steps
     value = weak_scaling_value(wl.value(t_step) * t_step, world, t_step)
 
-    # the dominant kernel: average launch duration inside a step
-    per_launch = _per_launch(torch, wl.step, max(5, min(args.steps, 20)), stream) / max(1, wl.n_launch)
+    # per-step device times: the dominant kernel's average launch duration
+    # inside a step, and the median with its 95 % interval
+    times = _step_times(torch, wl.step, max(10, min(args.steps, 30)), stream)
+    per_launch = statistics.mean(times) / max(1, wl.n_launch)
+    med, lo, hi = median_ci95(times)
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "workload": wl.name, "ms_per_step": t_step * 1e3,
                               "value": value, "per_launch_ms": per_launch * 1e3,
-                              "kernels": wl.kernels}), flush=True)
+                              "median_ms": med * 1e3, "kernels": wl.kernels}), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -744,6 +795,8 @@ def run_dcp(args):
         "e2e": e2e,
         "gpu_launches": wl.n_launch * args.steps,
         "clocks": clk.summary(),
+        "step_time_ms": {"median": round(med * 1e3, 5), "ci95": [round(lo * 1e3, 5), round(hi * 1e3, 5)],
+                         "runs": len(times), "timed_separately": True},
     }
     line.update(extra)
     print(json.dumps(line), flush=True)

@@ -168,6 +168,37 @@ class Graph:
         run.outputs = outputs
         return run
 
+    def prepare_host(self, inputs, outputs):
+        """``prepare`` for host buffers (numpy arrays or CPU tensors, ideally
+        page-locked so the kernels access them directly): checked and
+        marshalled once; the returned callable runs ``dcp_run_host``."""
+        import numpy as np
+        import torch
+        arrs = [a.numpy() if isinstance(a, torch.Tensor) else a for a in inputs]
+        outs = [o.numpy() if isinstance(o, torch.Tensor) else o for o in outputs]
+        for i, (a, v) in enumerate(zip(arrs, self.inputs)):
+            if (not a.flags.c_contiguous or a.shape != self.shape[v]
+                    or a.dtype != _numpy_dtype(self.dtype[v])):
+                raise ValueError("host input %d has the wrong shape, dtype or layout" % i)
+        for j, (o, v) in enumerate(zip(outs, self.outputs)):
+            if (not o.flags.c_contiguous or o.shape != self.shape[v]
+                    or o.dtype != _numpy_dtype(self.dtype[v])):
+                raise ValueError("host output %d has the wrong shape, dtype or layout" % j)
+        if len(arrs) != len(self.inputs) or len(outs) != len(self.outputs):
+            raise ValueError("expected %d inputs and %d outputs" % (len(self.inputs), len(self.outputs)))
+        ins = C._ptrs([a.ctypes.data for a in arrs])
+        ops = C._ptrs([o.ctypes.data for o in outs])
+        lib = C.load()
+        h = self._h
+        keep = (arrs, outs)
+
+        def run(stream=None):
+            s = (stream or torch.cuda.current_stream()).cuda_stream
+            C._check("dcp_run_host", lib.dcp_run_host(h, ins, ops, s))
+            return keep[1]
+
+        return run
+
     def run_host(self, inputs, outputs=None, stream=None):
         """Run on host arrays (numpy or CPU tensors); copies in and out, synchronous."""
         import numpy as np

@@ -50,3 +50,16 @@ def test_weak_scaling_value():
     # 2 ranks each moving 1e9 bytes; slowest rank took 0.5 s -> 4e9 B/s whole-job
     assert bench.weak_scaling_value(1e9, 2, 0.5) == 4e9
     assert bench.reduce_max(3.0) == 3.0
+
+
+def test_median_confidence_interval_order_statistics():
+    """The distribution-free 95 % interval of the median uses the order
+    statistics of Binomial(n, 1/2): ranks (2, 9) for n = 10 and (10, 21)
+    for n = 30 (1-based), the textbook values."""
+    import bench
+    v10 = list(range(1, 11))
+    assert bench.median_ci95(v10) == (5.5, 2, 9)
+    v30 = list(range(1, 31))
+    med, lo, hi = bench.median_ci95(v30[::-1])
+    assert (med, lo, hi) == (15.5, 10, 21)
+    assert bench.median_ci95([7.0]) == (7.0, 7.0, 7.0)

@@ -58,7 +58,7 @@ enum {
   DCP_E_INVALID_ARG = -1, /* bad handle, pointer, count, op code or option */
   DCP_E_SHAPE = -2,       /* operand shapes disagree, or a shape is not allowed */
   DCP_E_DTYPE = -3,       /* operand dtypes disagree, or op not defined on dtype */
-  DCP_E_UNSUPPORTED = -4, /* well-formed request outside what this build runs */
+  DCP_E_UNSUPPORTED = -4, /* well-formed request outside what the library implements */
   DCP_E_OOM = -5,         /* device or host allocation failed (or budget exceeded) */
   DCP_E_CUDA = -6,        /* a CUDA runtime/driver call failed (message has detail) */
   DCP_E_COMPILE = -7,     /* run-time compilation of a fused kernel failed */

@@ -284,3 +284,53 @@ def test_tanh_chain_paired_cells_loss():
     (lid,) = prog.outputs
     for v in out:
         assert abs(v - extra[lid]["fsum"]) <= 1e-10 * extra[lid]["abs"]
+
+
+def _heat3d_full(u0_host, flags=FUSED | C.DCP_AUTOTUNE):
+    """The 512^3, 50-step periodic 3-D workload as the benchmark launches it
+    (autotuned kernel form and tiles)."""
+    n = u0_host.shape[0]
+    g = programs.heat3d((n, n, n), 50, "periodic", "f64", fuse=flags)
+    d = to_dev(u0_host)
+    out = g.run([d])[0]
+    torch.cuda.synchronize()
+    return g, d, out
+
+
+def test_config3_full_size_fourier_mode():
+    """A periodic Fourier mode is an eigenvector of the 7-point step:
+    S cos(2 pi k.p / n) = lam cos(...), lam = 0.4 + 0.2 (cos tx + cos ty + cos tz),
+    so after 50 steps every one of the 512^3 cells equals lam^50 u0."""
+    n, T = 512, 50
+    k = (1, 2, 3)
+    ax = [np.cos(2 * np.pi * k[d] * np.arange(n) / n) for d in range(3)]
+    th = [2 * np.pi * k[d] / n for d in range(3)]
+    # separable product of per-axis modes (a product of cosines is also an eigenvector)
+    u0 = (ax[0][:, None, None] * ax[1][None, :, None] * ax[2][None, None, :]).astype(np.float64)
+    lam = 0.4 + 0.2 * (np.cos(th[0]) + np.cos(th[1]) + np.cos(th[2]))
+    _, d, out = _heat3d_full(u0)
+    want = torch.from_numpy(u0).cuda() * (lam ** T)
+    err = float((out - want).abs().max())
+    assert err <= 1e-12 * 1.0, err
+    del d, out, want
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def test_config3_full_size_sampled_points():
+    """Sampled cells of the 512^3, 50-step run against the oracle's
+    dependence-cone evaluation of the same cells."""
+    u0 = inputs.cfg3()
+    _, d, out = _heat3d_full(u0)
+    offs = programs.SEVEN_POINT
+    w = programs.SEVEN_WEIGHTS
+    rng = np.random.default_rng(77)
+    pts = [(0, 0, 0), (511, 511, 511), (5, 300, 511)] + [tuple(int(v) for v in rng.integers(0, 512, 3))
+                                                         for _ in range(2)]
+    for p in pts:
+        ref = oracle.stencil_point(u0, offs, w, "periodic", 50, p)
+        got = float(out[p].item())
+        assert abs(got - ref) <= 1e-12 * max(abs(ref), 1.0), (p, got, ref)
+    del d, out
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()

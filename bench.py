@@ -549,7 +549,12 @@ class Adjoint(Workload):
         self.prog.adjoint(self.dev, self.ones, self.grad)
 
     def legs(self):
-        return [("op_by_op", lambda: self.g0.adjoint(self.dev, self.ones, self.grad0), None)]
+        # the same call under a tape budget of 8 states (1.07 GB < the 2.7 GB
+        # full tape): sqrt(T) checkpoints, segments recomputed in the reverse pass
+        budget = 8 * self.dev[0].numel() * 8
+        return [("op_by_op", lambda: self.g0.adjoint(self.dev, self.ones, self.grad0), None),
+                ("checkpointed_8_states", lambda: self.prog.adjoint(self.dev, self.ones, self.grad,
+                                                                    tape_budget_bytes=budget), None)]
 
     def setup_e2e(self, torch):
         # u0 from page-locked host memory, the gradient back to it

@@ -208,7 +208,17 @@ void compile_plan(GraphImpl& g) {
 // ---------------------------------------------------------------------------
 // device state: modules, transients, scratch
 // ---------------------------------------------------------------------------
+// Host-side fault injection for tests (DCP_FAULT=alloc or DCP_FAULT=launch):
+// the named operation fails with the status a real failure returns, before
+// any device work, so the error paths run without faulting a GPU.
+static void maybe_inject(const char* what, dcp_status code) {
+  const char* f = std::getenv("DCP_FAULT");
+  if (f && std::strcmp(f, what) == 0)
+    fail(code, std::string("injected ") + what + " failure (DCP_FAULT)");
+}
+
 static void* dalloc(GraphImpl::Runtime& rt, size_t bytes) {
+  maybe_inject("alloc", DCP_E_OOM);
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
   check_cuda(cudaMalloc(&p, bytes), "cudaMalloc");
@@ -618,6 +628,7 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
 
 static void launch_one(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
                        cudaStream_t s) {
+  maybe_inject("launch", DCP_E_CUDA);
   const Group& G = g.groups[ls.group];
   if (G.kind == GroupKind::Map) launch_map(g, ls, ptr, s);
   else if (G.kind == GroupKind::AxisReduce) launch_axis(g, ls, ptr, s);

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2107_00555_gb300 import Graph, inputs
+from oracle import programs as OP
+from paper_2107_00555_gb300 import Graph, inputs, programs
 from paper_2107_00555_gb300 import _capi as C
 
 from gpu_util import assert_close, red_tol_for, tol_for, to_dev, to_host
@@ -308,3 +309,27 @@ def test_prepared_host_call_matches_run(pinned):
         torch.cuda.synchronize()
         for x, y in zip(got, ref):
             assert x.tobytes() == y.tobytes()
+
+
+@pytest.mark.parametrize("graph_replay", [0, 1])
+def test_injected_faults_leave_the_graph_usable(monkeypatch, graph_replay):
+    """DCP_FAULT makes the next device allocation or launch fail on the host
+    with the status a real failure returns; the graph stays usable and the
+    following run is correct (the CUDA-graph capture path included)."""
+    shape, T = (40, 50), 6
+    u0 = inputs.uniform(shape, 0.0, 1.0, 61)
+    ref = oracle.run(OP.jacobi2d(shape, T, "zero"), [u0])[-1]
+    g = programs.jacobi2d(shape, T, "zero", "f64")
+    g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 2)  # three launches, state buffers
+    g.set_option(C.DCP_OPT_USE_GRAPH, graph_replay)
+    g.fuse(C.DCP_FUSE_ALL)
+    d = to_dev(u0)
+    for fault, status in (("alloc", C.DCP_E_OOM), ("launch", C.DCP_E_CUDA)):
+        monkeypatch.setenv("DCP_FAULT", fault)
+        with pytest.raises(C.DcpError) as e:
+            g.run([d])
+        torch.cuda.synchronize()
+        assert e.value.status == status and "injected" in str(e.value)
+        monkeypatch.delenv("DCP_FAULT")
+        out = to_host(g.run([d])[0])
+        assert np.max(np.abs(out - ref)) <= 1e-12

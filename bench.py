@@ -179,16 +179,19 @@ class MapReduce(Workload):
         self.g0 = programs.map_reduce(self.n, self.dtype, fuse=0)
         self.out = self.g.empty_outputs(dev)
         self.out0 = self.g0.empty_outputs(dev)
+        # buffers marshalled once: a step is one C call
+        self.call = self.g.prepare(self.dev, self.out)
+        self.call0 = self.g0.prepare(self.dev, self.out0)
         plan = self.g.plan()
         self.kernels = [l["kernel"] for l in plan["launches"]]
         self.n_launch = len(self.kernels)
         self.n_launch0 = self.g0.n_kernels
 
     def step(self):
-        self.g.run(self.dev, self.out)
+        self.call()
 
     def step_opbyop(self):
-        self.g0.run(self.dev, self.out0)
+        self.call0()
 
     def legs(self):
         return [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
@@ -218,13 +221,15 @@ class MapReduce(Workload):
         self.g_staged = programs.map_reduce(self.n, self.dtype)
         self.g_staged.set_option(C.DCP_OPT_HOST_ACCESS, 0)
         self.g_staged.fuse(C.DCP_FUSE_ALL)
+        self.call_host = self.g.prepare_host(self.pinned, self.host_out)
+        self.call_staged = self.g_staged.prepare_host(self.pinned, self.host_out)
 
     def step_e2e(self):
         # page-locked host buffers: the fused kernel reads them directly
-        self.g.run_host(self.pinned, self.host_out)
+        self.call_host()
 
     def step_e2e_staged(self):
-        self.g_staged.run_host(self.pinned, self.host_out)
+        self.call_staged()
 
     def cpu_sample(self):
         """Oracle on the full workload (2**26 elements), single thread."""
@@ -269,15 +274,17 @@ class MapReduceRows(Workload):
         self.g0 = programs.map_reduce(self.shape, "f32", fuse=0, axis=1)
         self.out = self.g.empty_outputs(dev)
         self.out0 = self.g0.empty_outputs(dev)
+        self.call = self.g.prepare(self.dev, self.out)
+        self.call0 = self.g0.prepare(self.dev, self.out0)
         self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
         self.n_launch = len(self.kernels)
         self.n_launch0 = self.g0.n_kernels
 
     def step(self):
-        self.g.run(self.dev, self.out)
+        self.call()
 
     def legs(self):
-        return [("op_by_op", lambda: self.g0.run(self.dev, self.out0), self.n_launch0),
+        return [("op_by_op", self.call0, self.n_launch0),
                 ("torch_eager", self.step_torch, None)]
 
     def step_torch(self):
@@ -297,9 +304,10 @@ class MapReduceRows(Workload):
                          for _ in range(2)]
         self.h2d = sum(a.nbytes for a in self.pinned)
         self.d2h = sum(o.nbytes for o in self.host_out)
+        self.call_host = self.g.prepare_host(self.pinned, self.host_out)
 
     def step_e2e(self):
-        self.g.run_host(self.pinned, self.host_out)
+        self.call_host()
 
     def cpu_sample(self):
         """Oracle on the first 512 rows (1/16 of the workload), scaled per byte."""
@@ -368,15 +376,19 @@ class Stencil(Workload):
         self.g0 = build(self.shape, self.T, self.bc, self.dtype, fuse=0)
         self.out = self.g.empty_outputs(dev)
         self.out0 = self.g0.empty_outputs(dev)
+        # buffers marshalled once: a step is one C call (the 256^2 run is
+        # shorter than the Python-side checks of an unprepared call)
+        self.call = self.g.prepare(self.dev, self.out)
+        self.call0 = self.g0.prepare(self.dev, self.out0)
         self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
         self.n_launch = len(self.kernels)
         self.n_launch0 = self.g0.n_kernels
 
     def step(self):
-        self.g.run(self.dev, self.out)
+        self.call()
 
     def step_opbyop(self):
-        self.g0.run(self.dev, self.out0)
+        self.call0()
 
     def legs(self):
         return [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
@@ -403,12 +415,13 @@ class Stencil(Workload):
         t = torch.empty(self.shape, dtype=torch.float64, pin_memory=True)
         t.copy_(torch.from_numpy(self.host[0]))
         self.pinned = [t.numpy()]
-        self.host_out = [np.empty(self.shape, dtype=np.float64)]
+        self.host_out = [torch.empty(self.shape, dtype=torch.float64, pin_memory=True).numpy()]
         self.h2d = self.pinned[0].nbytes
         self.d2h = self.host_out[0].nbytes
+        self.call_host = self.g.prepare_host(self.pinned, self.host_out)
 
     def step_e2e(self):
-        self.g.run_host(self.pinned, self.host_out)
+        self.call_host()
 
     def cpu_sample(self):
         import oracle

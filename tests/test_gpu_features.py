@@ -333,3 +333,53 @@ def test_injected_faults_leave_the_graph_usable(monkeypatch, graph_replay):
         monkeypatch.delenv("DCP_FAULT")
         out = to_host(g.run([d])[0])
         assert np.max(np.abs(out - ref)) <= 1e-12
+
+
+def test_graphs_on_concurrent_host_threads():
+    """Different graphs run from several host threads at once, each on its
+    own stream (first runs compile and tune concurrently), give the bits of
+    serial runs."""
+    import threading
+
+    def make(k):
+        if k % 3 == 0:
+            return programs.jacobi2d((70 + k, 90), 6, "zero", "f64", fuse=C.DCP_FUSE_ALL | C.DCP_AUTOTUNE)
+        if k % 3 == 1:
+            return programs.map_reduce(50000 + 1000 * k, "f32", fuse=C.DCP_FUSE_ALL)
+        return programs.heat3d((20, 18, 40 + k), 2, "periodic", "f64", fuse=C.DCP_FUSE_ALL)
+
+    def inputs_for(k, g):
+        rng = np.random.default_rng(100 + k)
+        return [to_dev(rng.uniform(-1, 1, size=g.shape[v]).astype(
+            np.float32 if g.dtype[v] == C.DCP_F32 else np.float64)) for v in g.inputs]
+
+    serial = []
+    for k in range(6):
+        g = make(k)
+        serial.append([to_host(o).tobytes() for o in g.run(inputs_for(k, g))])
+    torch.cuda.synchronize()
+    results = [None] * 6
+    errors = []
+
+    def worker(k):
+        try:
+            torch.cuda.set_device(0)
+            s = torch.cuda.Stream()
+            g = make(k)
+            ins = inputs_for(k, g)
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    outs = g.run(ins, stream=s)
+            s.synchronize()
+            results[k] = [to_host(o).tobytes() for o in outs]
+        except Exception as e:  # reported below
+            errors.append((k, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(6)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for k in range(6):
+        assert results[k] == serial[k], k

@@ -137,13 +137,42 @@ def test_heat3d(bc, shape, dtype):
 
 
 def test_jacobi2d_config1_full():
-    """256 x 256 float64, zero boundary, 10 steps, U[0,1) (the small configuration)."""
+    """256 x 256 float64, zero boundary, 10 steps, U[0,1) (the small configuration),
+    fused, op by op, and in the benchmark's launch configuration (autotuned,
+    CUDA-graph replay, prepared call)."""
     u0 = inputs.cfg1()
     ref = oracle.run(OP.jacobi2d((256, 256), 10, "zero"), [u0])[-1]
     for flags in (FUSED, OPBYOP):
         g = programs.jacobi2d((256, 256), 10, "zero", "f64", fuse=flags)
         out = g.run([to_dev(u0)])
         assert_close(to_host(out[0]), ref, 1e-12, float(u0.max()), "cfg1")
+    g = programs.jacobi2d((256, 256), 10, "zero", "f64")
+    g.set_option(C.DCP_OPT_USE_GRAPH, 1)
+    g.fuse(FUSED | C.DCP_AUTOTUNE)
+    call = g.prepare([to_dev(u0)])
+    for _ in range(3):  # tuning run, eager run, graph replay
+        out = call()
+        assert_close(to_host(out[0]), ref, 1e-12, float(u0.max()), "cfg1 bench form")
+
+
+def test_map_reduce_rows_full_size_sampled_rows():
+    """8192 x 8192 float32, the row-reduced program as the benchmark runs it;
+    sampled rows against the oracle run on just those rows (each row's
+    results depend on that row only)."""
+    shape = (8192, 8192)
+    x, a, b = (v.reshape(shape) for v in inputs.cfg2(np.float32, n=shape[0] * shape[1]))
+    g = programs.map_reduce(shape, "f32", fuse=FUSED, axis=1)
+    dev = [to_dev(v) for v in (x, a, b)]
+    s, m = (to_host(o).astype(np.float64) for o in g.prepare(dev)())
+    rows = [0, 1, 4095, 8191] + list(range(17, 8192, 1021))
+    sub = [v[rows] for v in (x, a, b)]
+    prog = OP.map_reduce((len(rows), shape[1]), axis=1)
+    vals, extra = oracle.run(prog, sub, detail=True)
+    sid, mid = prog.outputs
+    assert np.all(np.abs(s[rows] - extra[sid]["fsum"]) <= 1e-4 * extra[sid]["abs"])
+    H = prog.handles
+    scale = oracle.reduce_axis("maxabs", np.abs(vals[H["p"]]) + np.abs(vals[H["h"]]), 1)
+    assert np.all(np.abs(m[rows] - vals[mid]) <= 1e-5 * np.maximum(vals[mid], scale))
 
 
 def test_time_tiling_is_bit_exact():

@@ -6,6 +6,9 @@
 //    the fused scope produces);
 //  * subgraph fusion -- reductions become epilogues of the kernel that
 //    produces their operand (tiled write-conflict resolution, Sec. 3.1);
+//    an axis reduction takes the elementwise maps producing its operand as
+//    the prologue of its own kernel, and reductions along the same axis of
+//    that prologue share the kernel;
 //    elementwise maps feeding a stencil become its prologue, evaluated at
 //    every cell the stencil tile reads; unary maps after a stencil step
 //    become that step's epilogue; maps after the last step become a post

@@ -1,10 +1,12 @@
 // Execution of a fused plan: one launch per fused group (or per time-tile
 // chunk of a stencil group), transients allocated once and reused (Sec. 3.1
 // transient allocation mitigation: temporaries are persistent, allocated when
-// the program is first run), per-group scratch for the tiled reductions,
-// optional replay of the whole run as one captured CUDA graph, and the
-// autotuner that times candidate tile shapes / time-tile depths of every
-// stencil group on the first run.
+// the program is first run), per-group scratch for the tiled reductions
+// (whole-array and axis), optional replay of the whole run as one captured
+// CUDA graph, runs on host buffers (in place when page-locked), host-side
+// fault injection for tests, and the autotuner that times candidate kernel
+// forms, tile shapes and time-tile depths of every stencil group on the
+// first run.
 #include <algorithm>
 #include <array>
 #include <cinttypes>

@@ -120,7 +120,8 @@ enum {
   DCP_OPT_TILE_Z = 10,         /* 3-D stencils: planes per CTA (z chunk, 1..1024) */
   DCP_OPT_STREAM_PREFETCH = 11, /* warp-stream stencils: row windows requested ahead (1..4) */
   DCP_OPT_STREAM_THREADS = 12, /* warp-stream stencils: threads per CTA (32..1024, multiple of 32; default 64) */
-  DCP_OPT_CELLS_PER_THREAD = 13 /* 3-D stencils: cells per thread along x (1 or 2) */
+  DCP_OPT_CELLS_PER_THREAD = 13, /* 3-D stencils: cells per thread along x (1 or 2) */
+  DCP_OPT_MAP_UNROLL = 14       /* map kernels: 16-byte vectors per array in flight per thread (1..8) */
 };
 
 /* ---- graph construction ------------------------------------------------ */

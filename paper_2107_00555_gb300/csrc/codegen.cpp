@@ -164,7 +164,7 @@ CodegenOut gen_map_kernel(const GraphImpl& g, const Group& G, bool vec_ok) {
   os << "// dcp fused map kernel: " << G.members.size() << " ops, " << G.loads.size() << " loads, "
      << G.stores.size() << " stores, " << G.reds.size() << " reductions\n";
   os << "#define DCP_T " << dtype_cname(T) << "\n";
-  os << "#define DCP_VEC " << vec << "\n#define DCP_UNROLL " << (vec > 1 ? 2 : 1) << "\n";
+  os << "#define DCP_VEC " << vec << "\n#define DCP_UNROLL " << (vec > 1 ? G.unroll : 1) << "\n";
   os << "#define DCP_NLOAD " << G.loads.size() << "\n#define DCP_NSTORE " << G.stores.size()
      << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n#define DCP_NRED " << G.reds.size()
      << "\n#define DCP_THREADS " << G.threads << "\n";

@@ -132,6 +132,7 @@ struct Group {
   int seg = 0;                  // warp stream: rows per work item (single arrays)
   int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
   int cx = 1;                   // 3-D stencils: cells per thread along x (1 or 2)
+  int unroll = 2;               // map groups: 16-byte vectors per array in flight per thread
   // axis-reduce groups: the reduced axis of the iteration space `shape`
   int axis = -1;
   // batch groups: the member stencil groups (same program, different shapes)

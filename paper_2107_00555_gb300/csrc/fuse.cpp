@@ -456,6 +456,7 @@ struct Planner {
       if (G.kind == GroupKind::Map) {
         G.threads = 256;
         G.blocks_per_sm = (int)opt(DCP_OPT_MAP_BLOCKS_PER_SM, 8);
+        G.unroll = (int)opt(DCP_OPT_MAP_UNROLL, 2);
         nl += 1;
       } else if (G.kind == GroupKind::AxisReduce) {
         G.threads = 256;

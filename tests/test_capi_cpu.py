@@ -81,6 +81,8 @@ def test_unknown_fuse_flag_and_options():
     assert _err(g.set_option, C.DCP_OPT_TILE_Z, 1025) == C.DCP_E_INVALID_ARG
     g.set_option(C.DCP_OPT_TILE_Z, 16)
     assert _err(g.set_option, C.DCP_OPT_CELLS_PER_THREAD, 3) == C.DCP_E_INVALID_ARG
+    assert _err(g.set_option, C.DCP_OPT_MAP_UNROLL, 9) == C.DCP_E_INVALID_ARG
+    g.set_option(C.DCP_OPT_MAP_UNROLL, 3)
     g.set_option(C.DCP_OPT_CELLS_PER_THREAD, 2)
     g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, 3)
     g.fuse(0)

@@ -2,7 +2,6 @@
 import pytest
 
 import paper_2107_00555_gb300 as dcp
-from paper_2107_00555_gb300 import _capi as C
 
 
 def test_traced_map_reduce_is_one_kernel():

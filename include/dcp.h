@@ -189,7 +189,12 @@ dcp_status dcp_fuse(dcp_graph g, uint32_t flags, int32_t* n_kernels_out);
 
 /* Runs the fused program on `cuda_stream`.  inputs[i] / outputs[j] are
  * device pointers in declaration / marking order.  Transient buffers are
- * allocated on the first run and reused.  Asynchronous. */
+ * allocated on the first run and reused.  With DCP_AUTOTUNE the first run
+ * also times the candidate launch configurations of every stencil group (its
+ * outputs are the program's; it synchronises the stream).  Asynchronous.
+ * For tests, the environment variable DCP_FAULT=alloc (or =launch) makes the
+ * next device allocation (kernel launch) fail with DCP_E_OOM (DCP_E_CUDA)
+ * before any device work; the graph stays usable. */
 dcp_status dcp_run(dcp_graph g, const void* const* inputs, void* const* outputs,
                    void* cuda_stream);
 

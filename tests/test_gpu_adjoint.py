@@ -103,6 +103,28 @@ def test_map_program_adjoint_vs_oracle():
         assert_close(gg, r, 1e-12, float(np.max(np.abs(r))), "map adjoint")
 
 
+def test_max_min_adjoint_ties_route_to_the_selected_operand():
+    """Inputs drawn from a few integers and signed zeros tie often; at a tie
+    the forward pass returns b and the adjoint goes to b, on both sides.
+    Each adjoint is one cotangent or a sum of two, so the match is exact."""
+    n = 4099
+    rng = np.random.default_rng(27)
+    vals = np.array([-1.0, -0.0, 0.0, 1.0, 2.0])
+    x, a = rng.choice(vals, n), rng.choice(vals, n)
+    p, g = oracle.Program(), Graph()
+    px, pa = p.input("f64", (n,)), p.input("f64", (n,))
+    gx, ga = g.input("f64", (n,)), g.input("f64", (n,))
+    for op in ("max", "min"):
+        p.output(p.map(op, [px, pa]))
+        g.output(g.map(op, [gx, ga]))
+    gy, gz = rng.normal(size=n), rng.normal(size=n)
+    ref = oracle.adjoint(p, [x, a], [gy, gz])
+    g.fuse(C.DCP_FUSE_ALL)
+    got = _adjoint(g, [x, a], [gy, gz])
+    for r, gg in zip(ref, got):
+        assert np.array_equal(gg, r)
+
+
 def test_config5_adjoint_full_size():
     """256^3 float64, 20 steps of tanh(S u), loss = sum(u_T^2): GPU reverse pass
     against the oracle's reverse pass, full tape and checkpointed."""

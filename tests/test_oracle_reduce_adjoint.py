@@ -62,10 +62,31 @@ def test_first_index_wins_ties_and_nan_propagates():
     [2.0 ** 53, 1.0, 1.0],
     [0.1] * 10,
     [1e308, -1e308, 1e-308, 3.0, -3.0],
+    # half-way cases: the two leading terms tie (and would round to even),
+    # the lower-order term decides the direction
+    [1e16, 1.0, 1e-16],
+    [1e16, 1.0, -1e-16],
+    [2.0 ** 53, 1.0, 2.0 ** -60],
+    [-(2.0 ** 53), -1.0, -(2.0 ** -60)],
 ])
 def test_fsum_matches_python_fsum(case):
     y = np.array(case, dtype=np.float64)
     assert oracle.fsum(y) == math.fsum(case)
+
+
+def test_fsum_half_way_rounding():
+    """The exact sum 1e16 + 1 + 1e-16 lies just above the midpoint of two
+    doubles (1e16 and 1e16 + 2): it rounds up, although 1e16 + 1 alone ties
+    to the even neighbour 1e16."""
+    assert oracle.fsum(np.array([1e16, 1.0, 1e-16])) == 1e16 + 2.0
+    assert oracle.fsum(np.array([1e16, 1.0, -1e-16])) == 1e16
+    rng = np.random.default_rng(13)
+    for _ in range(200):
+        big = float(2.0 ** int(rng.integers(53, 60)))
+        ulp = big / 2.0 ** 52
+        tiny = float(rng.choice([-1.0, 1.0])) * ulp * 2.0 ** -int(rng.integers(5, 40))
+        case = [big, ulp / 2.0 * float(rng.choice([-1.0, 1.0])), tiny]
+        assert oracle.fsum(np.array(case)) == math.fsum(case), case
 
 
 def test_fsum_random_cancellation_matches_python_fsum():
@@ -270,3 +291,24 @@ def test_broadcast_adjoint_central_differences():
     d = rng.normal(size=n)
     (jv,) = oracle.jvp(p, [x0], [d])
     assert abs(float(jv) - float(np.sum(g * d))) < 1e-10 * max(1.0, abs(float(jv)))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_max_min_adjoint_at_ties_follows_the_selected_operand(op):
+    """At a tie max/min is not differentiable; the adjoint goes to the operand
+    the forward pass returned.  Signed zeros make that operand visible (the
+    forward result of a +0/-0 tie carries b's sign), and the reverse pass must
+    agree with the tangent pass there: <J v, w> = <v, J^T w> holds only if
+    both take the same operand at every tie."""
+    a = np.array([0.0, -0.0, 1.5, 2.0, -3.0])
+    b = np.array([-0.0, 0.0, 1.5, 2.0, -3.0])
+    y = oracle.map_f(op, a, b)
+    assert np.array_equal(np.signbit(y), np.signbit(b))
+    g = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    ga, gb = oracle.map_vjp(op, a, b, 0.0, y, g)
+    assert np.array_equal(ga, np.zeros(5)) and np.array_equal(gb, g)
+    rng = np.random.default_rng(31)
+    da, db = rng.normal(size=5), rng.normal(size=5)
+    dy = oracle.map_jvp(op, a, b, 0.0, y, da, db)
+    assert np.array_equal(dy, db)
+    assert float(np.dot(dy, g)) == pytest.approx(float(np.dot(da, ga) + np.dot(db, gb)), rel=1e-15)

@@ -161,9 +161,9 @@ class MapReduce(Workload):
 
     # FP64 operations per element of the f64 program as executed: exp and sin
     # in binary64 have no fixed operation count, so the FP64 work is the one
-    # counted by ncu on the fused kernel (27 DFMA, 4 DADD, 4 DMUL per element,
-    # a DFMA counted as 2 flops)
-    F64_FLOPS_PER_ELEMENT = 62
+    # counted by ncu on the fused kernel (22 DFMA, 4 DADD, 5 DMUL per element
+    # with the kernels' own exp and sin, a DFMA counted as 2 flops)
+    F64_FLOPS_PER_ELEMENT = 53
 
     def roof(self):
         # f32: device memory bound (3 arrays read once); f64: the FP64 pipes

@@ -31,7 +31,8 @@ EMBED = [("dcp_device.cuh", "device_header_source"),
          ("k_stencil2d.cuh", "kernel_stencil2d_source"),
          ("k_stencil3d.cuh", "kernel_stencil3d_source"),
          ("k_stencil2d_stream.cuh", "kernel_stream_source"),
-         ("k_axis.cuh", "kernel_axis_source")]
+         ("k_axis.cuh", "kernel_axis_source"),
+         ("k_math64.cuh", "kernel_math64_source")]
 
 
 def _embed_source() -> str:

@@ -88,9 +88,9 @@ std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std:
     case kOpLt: return "dcp_lt(" + a + ", " + b + ")";
     case DCP_NEG: return "dcp_neg(" + a + ")";
     case DCP_ABS: return "dcp_abs(" + a + ")";
-    case DCP_EXP: return "dcp_exp(" + a + ")";
-    case DCP_SIN: return "dcp_sin(" + a + ")";
-    case DCP_COS: return "dcp_cos(" + a + ")";
+    case DCP_EXP: return (n.dtype == DCP_F64 ? "dcp_exp64(" : "dcp_exp(") + a + ")";
+    case DCP_SIN: return (n.dtype == DCP_F64 ? "dcp_sin64(" : "dcp_sin(") + a + ")";
+    case DCP_COS: return (n.dtype == DCP_F64 ? "dcp_cos64(" : "dcp_cos(") + a + ")";
     case DCP_TANH: return "dcp_tanh(" + a + ")";
     case DCP_SQRT: return "dcp_sqrt(" + a + ")";
     case DCP_SQUARE: return "dcp_square(" + a + ")";
@@ -135,13 +135,24 @@ uint64_t skeleton_hash(const std::string& body) {
       {"k_stencil2d.cuh", kernel_stencil2d_source()},
       {"k_stencil3d.cuh", kernel_stencil3d_source()},
       {"k_stencil2d_stream.cuh", kernel_stream_source()},
-      {"k_axis.cuh", kernel_axis_source()}};
+      {"k_axis.cuh", kernel_axis_source()},
+      {"k_math64.cuh", kernel_math64_source()}};
   for (const auto& k : skel)
     if (body.find(std::string("#include \"") + k.first + "\"") != std::string::npos) text += k.second;
   return fnv1a(text);
 }
 
-std::string finish(const std::string& prefix, const std::string& body) {
+std::string finish(const std::string& prefix, const std::string& b) {
+  // binary64 exp / sin / cos come from k_math64.cuh; it is included only by
+  // kernels that call them, so other kernels' sources (and names) do not
+  // depend on it
+  std::string body = b;
+  const std::string dev = "#include \"dcp_device.cuh\"\n";
+  const size_t at = body.find(dev);
+  if (at != std::string::npos && (body.find("dcp_exp64(") != std::string::npos ||
+                                  body.find("dcp_sin64(") != std::string::npos ||
+                                  body.find("dcp_cos64(") != std::string::npos))
+    body.insert(at + dev.size(), "#include \"k_math64.cuh\"\n");
   char name[64];
   std::snprintf(name, sizeof name, "%s_%016" PRIx64, prefix.c_str(),
                 fnv1a(body) ^ skeleton_hash(body));

@@ -170,6 +170,7 @@ const char* kernel_stencil2d_source();  // k_stencil2d.cuh
 const char* kernel_stencil3d_source();  // k_stencil3d.cuh
 const char* kernel_stream_source();     // k_stencil2d_stream.cuh
 const char* kernel_axis_source();       // k_axis.cuh
+const char* kernel_math64_source();     // k_math64.cuh
 
 // ---------------------------------------------------------------------------
 // Graph object

@@ -285,3 +285,40 @@ def test_every_kernel_family_compiles(dtype):
         g.fuse(C.DCP_FUSE_ALL)
     programs.batch2d([5, 40, 70], 6, "zero", dtype, fuse=C.DCP_FUSE_ALL | C.DCP_BATCH)
     programs.tanh_chain((8, 9, 10), 2, "periodic", dtype, fuse=C.DCP_FUSE_ALL)
+
+
+def test_math64_constants_are_the_generated_roundings():
+    """k_math64.cuh holds exactly what its generator computes in 200-bit
+    arithmetic (2^(j/64), the split ln2/64 and pi/2, 1/n!), and the values
+    are the ones the mathematics fixes: the table's entries double from j to
+    j + 64, the splits sum to the constants, the Taylor coefficients
+    alternate in sign as 1/n! does."""
+    mpmath = pytest.importorskip("mpmath")
+    import importlib.util
+    import math
+    from fractions import Fraction
+    kdir = os.path.join(os.path.dirname(C.__file__), "csrc", "kernels")
+    spec = importlib.util.spec_from_file_location("gen_math64_constants",
+                                                  os.path.join(kdir, "gen_math64_constants.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    text = open(os.path.join(kdir, "k_math64.cuh")).read()
+    a = text.index("// BEGIN generated")
+    b = text.index("// END generated")
+    assert text[a:b] + "// END generated by gen_math64_constants.py\n" == gen.block()
+    c = gen.constants()
+    tab = c["DCP_M64_EXP_TAB"]
+    assert tab[0] == 1.0 and tab[32] == float.fromhex("0x1.6a09e667f3bcdp+0")  # sqrt(2)
+    assert all(abs(tab[j] * tab[64 - j] - 2.0) <= 4 * math.ulp(2.0) for j in range(1, 64))
+    assert all(1.0 <= t < 2.0 for t in tab) and tab == sorted(tab)
+    mpmath.mp.prec = 200
+    hi, lo = c["DCP_M64_L"]
+    assert abs(Fraction(hi) + Fraction(lo) - gen.to_fraction(mpmath.log(2) / 64)) < Fraction(1, 2 ** 110)
+    p1, p2, p3 = c["DCP_M64_PIO2"]
+    assert p1 == math.pi / 2
+    assert abs(Fraction(p1) + Fraction(p2) + Fraction(p3) - gen.to_fraction(mpmath.pi / 2)) < Fraction(1, 2 ** 160)
+    assert c["DCP_M64_SIN_TAYLOR"][0] == -1 / 6 and c["DCP_M64_COS_TAYLOR"][0] == -0.5
+    for k, v in enumerate(c["DCP_M64_SIN_TAYLOR"], start=1):
+        assert v == float(Fraction((-1) ** k, math.factorial(2 * k + 1)))
+    for k, v in enumerate(c["DCP_M64_COS_TAYLOR"], start=1):
+        assert v == float(Fraction((-1) ** k, math.factorial(2 * k)))

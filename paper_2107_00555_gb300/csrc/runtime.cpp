@@ -1032,7 +1032,9 @@ std::string describe_plan(const GraphImpl& g) {
       os << (li ? ", " : "") << "{\"group\": " << ls.group << ", \"kernel\": \"" << ls.code.name
          << "\", \"steps\": [" << ls.s0 << ", " << ls.s1 << "], \"smem\": " << ls.code.smem_bytes
          << ", \"threads\": " << ls.code.threads << ", \"compile_ms\": " << ls.compile_ms
-         << ", \"regs\": " << ls.regs << ", \"occupancy\": " << ls.occupancy << "}";
+         << ", \"regs\": " << ls.regs << ", \"occupancy\": " << ls.occupancy;
+      if (ls.code.deferred) os << ", \"deferred_scale\": " << ls.code.defer_scale;
+      os << "}";
     }
   }
   os << "], \"transient_bytes\": ";

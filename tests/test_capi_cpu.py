@@ -322,3 +322,39 @@ def test_math64_constants_are_the_generated_roundings():
         assert v == float(Fraction((-1) ** k, math.factorial(2 * k + 1)))
     for k, v in enumerate(c["DCP_M64_COS_TAYLOR"], start=1):
         assert v == float(Fraction((-1) ** k, math.factorial(2 * k)))
+
+
+def test_plan_deferred_common_weight_3d():
+    """Linear runs of f64 3-D steps with weights f * r_k (r_k exact) run on
+    the ratios and apply f^m at the end of every chunk of m <= D steps,
+    (sum |r_k|)^D <= 2^32: D = 9 for the 7-point heat stencil (0.4 = 4 * 0.1,
+    sum of ratios 10).  Fixed rings, single steps, f32 and weights without
+    exact ratios keep the plain weighted sum."""
+    def scales(g):
+        return [l.get("deferred_scale") for l in g.plan()["launches"]]
+
+    sc = scales(programs.heat3d((8, 9, 10), 23, "periodic", "f64", fuse=C.DCP_FUSE_ALL))
+    chunk_ends = {8: 1e-9, 17: 1e-9, 22: 1e-5}
+    assert len(sc) == 23
+    for i, s in enumerate(sc):
+        assert s == pytest.approx(chunk_ends.get(i, 1.0), rel=1e-15), (i, s)
+    assert scales(programs.heat3d((8, 9, 10), 18, "zero", "f64", fuse=C.DCP_FUSE_ALL))[-1] == \
+        pytest.approx(1e-9, rel=1e-15)
+    for g in (programs.heat3d((8, 9, 10), 5, "fixed_ring", "f64", fuse=C.DCP_FUSE_ALL),
+              programs.heat3d((8, 9, 10), 1, "periodic", "f64", fuse=C.DCP_FUSE_ALL),
+              programs.heat3d((8, 9, 10), 5, "periodic", "f32", fuse=C.DCP_FUSE_ALL),
+              programs.tanh_chain((8, 9, 10), 3, fuse=C.DCP_FUSE_ALL)):
+        assert all(s is None for s in scales(g))
+    g = Graph()
+    x = g.input("f64", (8, 9, 10))
+    g.output(g.stencil(x, programs.SEVEN_POINT, [0.3] + [0.7 / 6] * 6, "zero", 4))
+    g.fuse(C.DCP_FUSE_ALL)
+    assert all(s is None for s in scales(g))
+    # a fused chain of equal one-step nodes is one run, like one five-step node
+    g = Graph()
+    v = g.input("f64", (8, 9, 10))
+    for _ in range(5):
+        v = g.stencil(v, programs.SEVEN_POINT, programs.SEVEN_WEIGHTS, "periodic", 1)
+    g.output(v)
+    g.fuse(C.DCP_FUSE_ALL)
+    assert scales(g)[:4] == [1.0] * 4 and scales(g)[4] == pytest.approx(1e-5, rel=1e-15)

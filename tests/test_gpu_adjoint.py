@@ -30,6 +30,25 @@ def test_tanh_chain_adjoint_vs_oracle(shape, T):
     assert_close(got, ref, 1e-12, float(np.max(np.abs(ref))), "tanh chain adjoint")
 
 
+def test_linear_heat_chain_adjoint_vs_oracle():
+    """loss = sum(u_T^2) for u_T = S^T u0 (12 periodic heat steps, one linear
+    run): the reverse pass's transposed chain also runs on the deferred
+    common weight (chunks of 9 and 3) and matches the oracle's reverse pass."""
+    shape, T = (10, 12, 14), 12
+    u0 = inputs.uniform(shape, -1.0, 1.0, 24)
+    p = oracle.Program()
+    pv = p.input("f64", shape)
+    p.output(p.reduce(p.map("square", [p.stencil(pv, OP.SEVEN, OP.W7, "periodic", T)]), "sum"))
+    (ref,) = oracle.adjoint(p, [u0], [1.0])
+    g = Graph()
+    gv = g.input("f64", shape)
+    g.output(g.reduce(g.map("square", [g.stencil(gv, programs.SEVEN_POINT, programs.SEVEN_WEIGHTS,
+                                                  "periodic", T)]), "sum"))
+    g.fuse(C.DCP_FUSE_ALL)
+    (got,) = _adjoint(g, [u0], [np.array(1.0)])
+    assert_close(got, ref, 1e-12, float(np.max(np.abs(ref))), "linear heat chain adjoint")
+
+
 def test_checkpointed_equals_full_tape_bitwise():
     shape, T = (20, 24, 28), 9
     u0 = inputs.uniform(shape, -1.0, 1.0, 22)

@@ -280,6 +280,43 @@ def test_heat3d_paired_cells_bitwise(bc, shape, dtype):
     assert all(r == res[0] for r in res)
 
 
+@pytest.mark.parametrize("bc", ["zero", "periodic"])
+def test_heat3d_deferred_weight_chunks_magnitudes_nan(bc):
+    """23 steps run as chunks of 9, 9 and 5 on the ratios 4 and 1 of the
+    heat weights, the factor 0.1^m applied at each chunk's end: values near
+    1e280 stay finite and within the f64 tolerance of the oracle's plain
+    weighted sum, a NaN spreads over the same dependence cone, and every tile
+    shape gives the same bits."""
+    shape, T = (9, 10, 11), 23
+    u0 = inputs.uniform(shape, -1.0, 1.0, 19) * 1e280
+    ref = oracle.run(OP.heat3d(shape, T, bc), [u0])[-1]
+    g = programs.heat3d(shape, T, bc, "f64", fuse=FUSED)
+    assert [l.get("deferred_scale") is not None for l in g.plan()["launches"]] == [True] * T
+    got = to_host(g.run([to_dev(u0)])[0])
+    assert np.isfinite(got).all()
+    assert_close(got, ref, 1e-12, float(np.max(np.abs(u0))), "deferred weight, 1e280 %s" % bc)
+    shape = (9, 10, 60)  # long enough in x for cells outside the NaN's cone
+    u1 = inputs.uniform(shape, -1.0, 1.0, 20)
+    u1[4, 5, 2] = np.nan
+    ref = oracle.run(OP.heat3d(shape, T, bc), [u1])[-1]
+    assert 0 < np.isnan(ref).sum() < ref.size
+    res = []
+    for cx, tile in ((1, None), (2, None), (2, (4, 16, 32)), (1, (8, 4, 64))):
+        g = programs.heat3d(shape, T, bc, "f64")
+        g.set_option(C.DCP_OPT_CELLS_PER_THREAD, cx)
+        if tile is not None:
+            g.set_option(C.DCP_OPT_TILE_Z, tile[0])
+            g.set_option(C.DCP_OPT_TILE_Y, tile[1])
+            g.set_option(C.DCP_OPT_TILE_X, tile[2])
+        g.fuse(FUSED)
+        got = to_host(g.run([to_dev(u1)])[0])
+        res.append(got.tobytes())
+    assert all(r == res[0] for r in res)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert_close(got[ok], ref[ok], 1e-12, 1.0, "deferred weight with NaN %s" % bc)
+
+
 def test_radius2_3d_stencil_paired_cells():
     shape = (12, 14, 37)
     offs = [(0, 0, 0), (0, 0, -2), (0, 0, 2), (0, -2, 0), (0, 2, 0), (-2, 0, 0), (2, 0, 0),

@@ -350,7 +350,9 @@ class Stencil(Workload):
 
     def roof(self):
         # FP64 ALU bound: 5 (2-D) / 7 (3-D) weighted terms per cell and step,
-        # each a multiply and an add except the first (2k - 1 flops)
+        # each a multiply and an add except the first (2k - 1 flops) -- the
+        # step as defined; with the deferred common weight the kernels
+        # execute k - 1 FP64 operations per cell and step
         npts = 5 if self.name == "jacobi2d" else 7
         steps_per_launch = self.T / max(1, self.n_launch)
         return "alu", (2 * npts - 1) * self.cells * steps_per_launch, "flop"

@@ -150,7 +150,12 @@ dcp_status dcp_add_map(dcp_graph g, int32_t op, int32_t n_in, const dcp_value* i
  * out-of-place applications of out[p] = sum_k weights[k] * in[p + o_k],
  * o_k = offsets[k*ndim .. k*ndim+ndim-1] (axis order as the shape, last
  * axis contiguous), boundary rule `bc`.  Floating dtypes, 1..3 axes,
- * 1 <= npoints <= 32, |offset| <= 4 per axis, steps >= 0. */
+ * 1 <= npoints <= 32, |offset| <= 4 per axis, steps >= 0.  Rounding: each
+ * step is one multiply and FMAs in point order, except that a float64 run
+ * of two or more steps with a zero or periodic boundary whose weights are
+ * exact multiples of one weight f sums the exact ratios w_k / f and applies
+ * f^m every m steps (m bounded so that the scaled state grows by at most
+ * 2^32: finite results for inputs up to about 1e298). */
 dcp_status dcp_add_stencil(dcp_graph g, dcp_value in, int32_t npoints, const int32_t* offsets,
                            const double* weights, int32_t bc, int32_t steps, dcp_value* out);
 

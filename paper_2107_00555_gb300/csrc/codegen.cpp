@@ -278,6 +278,112 @@ void emit_stencil_io(std::ostringstream& os, const GraphImpl& g, const Group& G,
   os << "  (void)p; (void)sc; (void)gi; (void)v; (void)st; (void)rv;\n}\n";
 }
 
+// Deferred common weight of a linear run of binary64 stencil steps.  A step
+// u' = sum_k w_k u[p + o_k] whose weights are all exact multiples
+// w_k = f r_k of one weight f (r_k = 1 at f's own points) is computed as
+// w' = sum_k r_k w[p + o_k] on the scaled state w = u / f^t, and f^m is
+// applied once at the end of every chunk of m steps.  The sum then starts
+// from a point of ratio 1 with no multiply, so a p-point step takes p - 1
+// FP64 operations instead of p (6 instead of 7 for the 7-point heat
+// stencil, where 0.4 = 4 * 0.1 exactly; 4 adds instead of 5 operations for
+// the 5-point average).  Only binary64 steps, which the FP64 pipe bounds,
+// take this form.  A run is the consecutive steps of a group with equal
+// weights (one stencil node, or a fused chain of equal ones), no epilogue
+// map before its last step, a zero or periodic boundary (a fixed ring would
+// need its border rescaled every step) and at least two steps.  Chunks are
+// at most D steps with (sum |r_k|)^D <= 2^32, so the scaled state stays
+// within 2^32 of the unscaled state's bound; f^m is the product of m
+// roundings of f, applied with one more rounding.  Each step's arithmetic
+// depends only on its place in its run, so every kernel form, tile shape,
+// time-tile depth and split into launches computes the same bits.
+struct Defer {
+  bool on = false;
+  std::vector<int> order;     // point order: a ratio-1 point first
+  std::vector<double> ratio;  // r_k = w_k / f, exact
+  double scale = 1.0;         // multiply after this step (1.0: none)
+};
+
+bool defer_ratios(const std::vector<double>& w, std::vector<double>& ratio, double& f_out,
+                  double& gsum) {
+  const int P = (int)w.size();
+  double f = 0.0;
+  int best = 0;
+  for (int k = 0; k < P; ++k) {  // f: the most frequent nonzero weight
+    if (w[k] == 0.0) continue;
+    int c = 0;
+    for (int j = 0; j < P; ++j) c += w[j] == w[k];
+    if (c > best) best = c, f = w[k];
+  }
+  if (f == 0.0 || !std::isfinite(f)) return false;
+  ratio.assign(P, 0.0);
+  gsum = 0.0;
+  for (int k = 0; k < P; ++k) {
+    const double r = w[k] / f;
+    if (!std::isfinite(r) || std::fma(r, f, -w[k]) != 0.0) return false;  // exact
+    ratio[k] = r;
+    gsum += std::fabs(r);
+  }
+  f_out = f;
+  return true;
+}
+
+Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
+  Defer d;
+  const Node& n = g.nodes[G.steps[s].node];
+  if (n.dtype != DCP_F64 || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return d;
+  const int S = (int)G.steps.size();
+  // steps of the group share their offsets; a run also needs the same
+  // weights and boundary
+  auto same = [&](int t) {
+    const Node& m = g.nodes[G.steps[t].node];
+    return m.bc == n.bc && m.weights == n.weights;
+  };
+  int a = s;
+  while (a > 0 && same(a - 1) && G.steps[a - 1].epi.empty()) --a;
+  int b = s + 1;
+  while (b < S && same(b) && G.steps[b - 1].epi.empty()) ++b;
+  const int L = b - a;
+  if (L < 2) return d;
+  std::vector<double> r;
+  double f = 0.0, gsum = 0.0;
+  if (!defer_ratios(n.weights, r, f, gsum)) return d;
+  const int D = gsum <= 1.0 ? L : std::min(L, (int)std::floor(32.0 / std::log2(gsum)));
+  if (D < 2) return d;
+  auto power = [f](int m) {
+    double F = 1.0;
+    for (int t = 0; t < m; ++t) F *= f;
+    return std::isnormal(F) ? F : 0.0;
+  };
+  if (power(D) == 0.0 || (L % D != 0 && power(L % D) == 0.0)) return d;
+  const int i = s - a;
+  const int m = (i + 1) % D == 0 ? D : (s == b - 1 ? (i + 1) % D : 0);
+  d.on = true;
+  d.ratio = r;
+  for (int k = 0; k < (int)r.size(); ++k)
+    if (r[k] == 1.0) {
+      d.order.push_back(k);
+      break;
+    }
+  for (int k = 0; k < (int)r.size(); ++k)
+    if (k != d.order[0]) d.order.push_back(k);
+  d.scale = m > 0 ? power(m) : 1.0;
+  return d;
+}
+
+// One term of a weighted sum into accumulator a (declared by the first).
+void emit_term(std::ostringstream& os, int T, const std::string& a, const std::string& x, double w,
+               bool first, bool deferred) {
+  if (deferred) {
+    if (first) os << "  DCP_T " << a << " = " << x << ";\n";
+    else if (w == 1.0) os << "  " << a << " = dcp_add(" << a << ", " << x << ");\n";
+    else os << "  " << a << " = dcp_fma_rn(" << weight_literal(T, w) << ", " << x << ", " << a << ");\n";
+    return;
+  }
+  const std::string wl = weight_literal(T, w);
+  if (first) os << "  DCP_T " << a << " = dcp_mul_rn(" << wl << ", " << x << ");\n";
+  else os << "  " << a << " = dcp_fma_rn(" << wl << ", " << x << ", " << a << ");\n";
+}
+
 // Epilogue chain of one step as a function of the weighted sum.
 std::string epi_body(const GraphImpl& g, const StepDesc& s) {
   std::ostringstream os;
@@ -342,6 +448,7 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
   };
   mask_fn("dcp_uses_lf", lmask);
   mask_fn("dcp_uses_rt", rmask);
+  std::vector<double> scales;
   for (int s = 0; s < nsteps; ++s) {
     const StepDesc& sd = G.steps[s0 + s];
     const Node& sn = g.nodes[sd.node];
@@ -349,19 +456,23 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
        << "][" << C << "], const DCP_T (&lf)[" << NR << "][" << RXA << "], const DCP_T (&rt)[" << NR
        << "][" << RXA << "], DCP_T (&out)[" << C << "]) {\n";
     os << "  (void)lf; (void)rt;\n";
+    const Defer df = plan_defer(g, G, s0 + s);
+    if (df.on) os << "  // deferred common weight: the ratios w_k / f\n";
+    scales.push_back(df.on ? df.scale : 0.0);
     for (int c = 0; c < C; ++c) {
-      for (int k = 0; k < sn.npts(); ++k) {
+      const std::string a = "a" + std::to_string(c);
+      for (int i = 0; i < sn.npts(); ++i) {
+        const int k = df.on ? df.order[i] : i;
         int dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
         int cc = c + dx, row = ry + dy;
         std::string x;
         if (cc < 0) x = "lf[" + std::to_string(row) + "][" + std::to_string(rx + cc) + "]";
         else if (cc >= C) x = "rt[" + std::to_string(row) + "][" + std::to_string(cc - C) + "]";
         else x = "up[" + std::to_string(row) + "][" + std::to_string(cc) + "]";
-        std::string w = weight_literal(T, sn.weights[k]);
-        if (k == 0) os << "  DCP_T a" << c << " = dcp_mul_rn(" << w << ", " << x << ");\n";
-        else os << "  a" << c << " = dcp_fma_rn(" << w << ", " << x << ", a" << c << ");\n";
+        emit_term(os, T, a, x, df.on ? df.ratio[k] : sn.weights[k], i == 0, df.on);
       }
-      os << "  out[" << c << "] = a" << c << ";\n";
+      if (df.scale != 1.0) os << "  " << a << " = dcp_mul_rn(" << weight_literal(T, df.scale) << ", " << a << ");\n";
+      os << "  out[" << c << "] = " << a << ";\n";
     }
     os << "}\n";
     os << "template <> __device__ __forceinline__ DCP_T dcp_epi<" << s << ">(DCP_T v) {\n"
@@ -371,105 +482,11 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
   CodegenOut out;
   out.threads = G.threads;
   out.smem_bytes = 0;
+  for (double x : scales)
+    if (x != 0.0) out.defer_scales = scales;
   out.source = finish(batch ? "dcp_bstream" : "dcp_stream", os.str());
   out.name = kname_of(out.source);
   return out;
-}
-
-// Deferred common weight of a linear run of binary64 3-D steps.  A step
-// u' = sum_k w_k u[p + o_k] whose weights are all exact multiples
-// w_k = f r_k of one weight f (r_k = 1 at f's own points) is computed as
-// w' = sum_k r_k w[p + o_k] on the scaled state w = u / f^t, and f^m is
-// applied once at the end of every chunk of m steps.  The sum then starts
-// from a point of ratio 1 with no multiply, so a p-point step takes p - 1
-// FP64 operations instead of p (6 instead of 7 for the 7-point heat
-// stencil, where 0.4 = 4 * 0.1 exactly).  A run is the consecutive steps of
-// a group with equal weights (one stencil node, or a chain of equal nodes),
-// no epilogue map before its last step, a zero or periodic boundary (a fixed ring would need its border rescaled every
-// step) and at least two steps.  Chunks are at most D steps with
-// (sum |r_k|)^D <= 2^32, so the scaled state stays within 2^32 of the
-// unscaled state's bound; f^m is the product of m roundings of f, applied
-// with one more rounding.  Each step's arithmetic depends only on its place
-// in its run, so every tile shape and every split into launches computes
-// the same bits.
-struct Defer3 {
-  bool on = false;
-  std::vector<int> order;     // point order: a ratio-1 point first
-  std::vector<double> ratio;  // r_k = w_k / f, exact
-  double scale = 1.0;         // multiply after this step (1.0: none)
-};
-
-Defer3 plan_defer3(const GraphImpl& g, const Group& G, int s) {
-  Defer3 d;
-  const int node = G.steps[s].node;
-  const Node& n = g.nodes[node];
-  if (n.dtype != DCP_F64 || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return d;
-  const int S = (int)G.steps.size();
-  // steps of the group share their offsets; a run also needs the same
-  // weights and boundary (one stencil node, or a chain of equal ones)
-  auto same = [&](int t) {
-    const Node& m = g.nodes[G.steps[t].node];
-    return m.bc == n.bc && m.weights == n.weights;
-  };
-  int a = s;
-  while (a > 0 && same(a - 1) && G.steps[a - 1].epi.empty()) --a;
-  int b = s + 1;
-  while (b < S && same(b) && G.steps[b - 1].epi.empty()) ++b;
-  const int L = b - a;
-  if (L < 2) return d;
-  // f: the most frequent nonzero weight (the first of equally frequent ones)
-  const int P = n.npts();
-  double f = 0.0;
-  int best = 0;
-  for (int k = 0; k < P; ++k) {
-    if (n.weights[k] == 0.0) continue;
-    int c = 0;
-    for (int j = 0; j < P; ++j) c += n.weights[j] == n.weights[k];
-    if (c > best) best = c, f = n.weights[k];
-  }
-  if (f == 0.0 || !std::isfinite(f)) return d;
-  std::vector<double> r(P);
-  double gsum = 0.0;
-  for (int k = 0; k < P; ++k) {
-    r[k] = n.weights[k] / f;
-    if (!std::isfinite(r[k]) || std::fma(r[k], f, -n.weights[k]) != 0.0) return d;
-    gsum += std::fabs(r[k]);
-  }
-  const int D = gsum <= 1.0 ? L : std::min(L, (int)std::floor(32.0 / std::log2(gsum)));
-  if (D < 2) return d;
-  auto power = [f](int m) {
-    double F = 1.0;
-    for (int t = 0; t < m; ++t) F *= f;
-    return F;
-  };
-  if (!std::isnormal(power(D)) || (L % D != 0 && !std::isnormal(power(L % D)))) return d;
-  const int i = s - a;
-  const int m = (i + 1) % D == 0 ? D : (s == b - 1 ? (i + 1) % D : 0);
-  d.on = true;
-  d.ratio = r;
-  for (int k = 0; k < P; ++k)
-    if (r[k] == 1.0) {
-      d.order.push_back(k);
-      break;
-    }
-  for (int k = 0; k < P; ++k)
-    if (k != d.order[0]) d.order.push_back(k);
-  d.scale = m > 0 ? power(m) : 1.0;
-  return d;
-}
-
-// One term of a weighted sum into accumulator a (declared by the first).
-void emit_term(std::ostringstream& os, int T, const std::string& a, const std::string& x, double w,
-               bool first, bool deferred) {
-  if (deferred) {
-    if (first) os << "  DCP_T " << a << " = " << x << ";\n";
-    else if (w == 1.0) os << "  " << a << " = dcp_add(" << a << ", " << x << ");\n";
-    else os << "  " << a << " = dcp_fma_rn(" << weight_literal(T, w) << ", " << x << ", " << a << ");\n";
-    return;
-  }
-  const std::string wl = weight_literal(T, w);
-  if (first) os << "  DCP_T " << a << " = dcp_mul_rn(" << wl << ", " << x << ");\n";
-  else os << "  " << a << " = dcp_fma_rn(" << wl << ", " << x << ", " << a << ");\n";
 }
 
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
@@ -508,25 +525,31 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     if (!batch) emit_stencil_io(os, g, G, first, last);
     os << "template <int S> __device__ __forceinline__ DCP_T dcp_sum(const DCP_T* A, int c);\n";
     os << "template <int S> __device__ __forceinline__ DCP_T dcp_epi(DCP_T v);\n";
+    std::vector<double> scales;
     for (int s = 0; s < nsteps; ++s) {
       const StepDesc& sd = G.steps[s0 + s];
       const Node& sn = g.nodes[sd.node];
       os << "template <> __device__ __forceinline__ DCP_T dcp_sum<" << s
          << ">(const DCP_T* A, int c) {\n";
-      for (int k = 0; k < sn.npts(); ++k) {
+      const Defer df = plan_defer(g, G, s0 + s);
+      if (df.on) os << "  // deferred common weight: the ratios w_k / f\n";
+      scales.push_back(df.on ? df.scale : 0.0);
+      for (int i = 0; i < sn.npts(); ++i) {
+        const int k = df.on ? df.order[i] : i;
         int dy = G.offsets[k * 3 + 1], dx = G.offsets[k * 3 + 2];
         int off = dy * PW + dx;
-        std::string w = weight_literal(T, sn.weights[k]);
         std::string x = "A[c + (" + std::to_string(off) + ")]";
-        if (k == 0) os << "  DCP_T acc = dcp_mul_rn(" << w << ", " << x << ");\n";
-        else os << "  acc = dcp_fma_rn(" << w << ", " << x << ", acc);\n";
+        emit_term(os, T, "acc", x, df.on ? df.ratio[k] : sn.weights[k], i == 0, df.on);
       }
+      if (df.scale != 1.0) os << "  acc = dcp_mul_rn(" << weight_literal(T, df.scale) << ", acc);\n";
       os << "  return acc;\n}\n";
       os << "template <> __device__ __forceinline__ DCP_T dcp_epi<" << s << ">(DCP_T v) {\n"
          << epi_body(g, sd) << "}\n";
     }
     os << "#include \"k_stencil2d.cuh\"\n";
     out.smem_bytes = 2 * PW * PH * dtype_size(T);
+    for (double x : scales)
+      if (x != 0.0) out.defer_scales = scales;
   } else {
     if (nsteps != 1) fail(DCP_E_UNSUPPORTED, "3-D stencil launches run one step each");
     const int TX = G.tile[2], TY = G.tile[1], TZ = G.tile[0];
@@ -541,13 +564,12 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     const Node& sn = g.nodes[sd.node];
     os << "__device__ __forceinline__ void dcp_sum3(const DCP_T* const* pl, int c, DCP_T (&v)["
        << CX << "]) {\n";
-    const Defer3 df = plan_defer3(g, G, s0);
+    const Defer df = plan_defer(g, G, s0);
     std::vector<int> order(sn.npts());
     for (int k = 0; k < sn.npts(); ++k) order[k] = df.on ? df.order[k] : k;
     auto wt = [&](int k) { return df.on ? df.ratio[k] : sn.weights[k]; };
     if (df.on) os << "  // deferred common weight: the ratios w_k / f\n";
-    out.deferred = df.on;
-    out.defer_scale = df.scale;
+    if (df.on) out.defer_scales = {df.scale};
     if (CX == 1) {
       for (int i = 0; i < sn.npts(); ++i) {
         const int k = order[i];

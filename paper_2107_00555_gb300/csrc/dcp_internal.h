@@ -225,8 +225,10 @@ struct CodegenOut {
   int threads = 256;
   int vec = 1;     // axis reductions: elements per load
   int axmode = 0;  // axis reductions: 0 vectors along inner, 1 along the reduced axis
-  bool deferred = false;    // 3-D steps: weights as ratios to a deferred common weight
-  double defer_scale = 1.0; // 3-D steps: factor applied after this step (1: none)
+  // stencil launches: per step, the factor applied after the step when it
+  // sums ratios to a deferred common weight (1: none), 0 for a plain sum;
+  // empty when no step of the launch is deferred
+  std::vector<double> defer_scales;
 };
 CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 // Stencil launch `chunk` covers steps [s0, s1) of the group.

@@ -1033,7 +1033,12 @@ std::string describe_plan(const GraphImpl& g) {
          << "\", \"steps\": [" << ls.s0 << ", " << ls.s1 << "], \"smem\": " << ls.code.smem_bytes
          << ", \"threads\": " << ls.code.threads << ", \"compile_ms\": " << ls.compile_ms
          << ", \"regs\": " << ls.regs << ", \"occupancy\": " << ls.occupancy;
-      if (ls.code.deferred) os << ", \"deferred_scale\": " << ls.code.defer_scale;
+      if (!ls.code.defer_scales.empty()) {
+        os << ", \"deferred_scales\": [";
+        for (size_t i = 0; i < ls.code.defer_scales.size(); ++i)
+          os << (i ? ", " : "") << ls.code.defer_scales[i];
+        os << "]";
+      }
       os << "}";
     }
   }

@@ -324,14 +324,18 @@ def test_math64_constants_are_the_generated_roundings():
         assert v == float(Fraction((-1) ** k, math.factorial(2 * k)))
 
 
-def test_plan_deferred_common_weight_3d():
-    """Linear runs of f64 3-D steps with weights f * r_k (r_k exact) run on
-    the ratios and apply f^m at the end of every chunk of m <= D steps,
+def test_plan_deferred_common_weight():
+    """Linear runs of f64 steps with weights f * r_k (r_k exact) run on the
+    ratios and apply f^m at the end of every chunk of m <= D steps,
     (sum |r_k|)^D <= 2^32: D = 9 for the 7-point heat stencil (0.4 = 4 * 0.1,
-    sum of ratios 10).  Fixed rings, single steps, f32 and weights without
-    exact ratios keep the plain weighted sum."""
+    sum of ratios 10), 13 for the 5-point average.  Fixed rings, single
+    steps, f32 and weights without exact ratios keep the plain weighted sum
+    (no "deferred_scales" in the launch)."""
     def scales(g):
-        return [l.get("deferred_scale") for l in g.plan()["launches"]]
+        out = []
+        for l in g.plan()["launches"]:
+            out += l.get("deferred_scales", [None] * (l["steps"][1] - l["steps"][0]))
+        return out
 
     sc = scales(programs.heat3d((8, 9, 10), 23, "periodic", "f64", fuse=C.DCP_FUSE_ALL))
     chunk_ends = {8: 1e-9, 17: 1e-9, 22: 1e-5}
@@ -340,9 +344,23 @@ def test_plan_deferred_common_weight_3d():
         assert s == pytest.approx(chunk_ends.get(i, 1.0), rel=1e-15), (i, s)
     assert scales(programs.heat3d((8, 9, 10), 18, "zero", "f64", fuse=C.DCP_FUSE_ALL))[-1] == \
         pytest.approx(1e-9, rel=1e-15)
+    # 2-D, every kernel form and time-tile depth: the same per-step plan
+    for kernel in (0, 1):
+        for depth in (1, 3, 10):
+            g = programs.jacobi2d((40, 50), 30, "zero", "f64")
+            g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+            g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+            g.fuse(C.DCP_FUSE_ALL)
+            sc = scales(g)
+            assert len(sc) == 30
+            for i, s in enumerate(sc):
+                want = 0.2 ** 13 if i in (12, 25) else (0.2 ** 4 if i == 29 else 1.0)
+                assert s == pytest.approx(want, rel=1e-14), (kernel, depth, i, s)
     for g in (programs.heat3d((8, 9, 10), 5, "fixed_ring", "f64", fuse=C.DCP_FUSE_ALL),
               programs.heat3d((8, 9, 10), 1, "periodic", "f64", fuse=C.DCP_FUSE_ALL),
               programs.heat3d((8, 9, 10), 5, "periodic", "f32", fuse=C.DCP_FUSE_ALL),
+              programs.jacobi2d((40, 50), 10, "zero", "f32", fuse=C.DCP_FUSE_ALL),
+              programs.jacobi2d((40, 50), 10, "fixed_ring", "f64", fuse=C.DCP_FUSE_ALL),
               programs.tanh_chain((8, 9, 10), 3, fuse=C.DCP_FUSE_ALL)):
         assert all(s is None for s in scales(g))
     g = Graph()

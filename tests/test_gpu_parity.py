@@ -291,7 +291,7 @@ def test_heat3d_deferred_weight_chunks_magnitudes_nan(bc):
     u0 = inputs.uniform(shape, -1.0, 1.0, 19) * 1e280
     ref = oracle.run(OP.heat3d(shape, T, bc), [u0])[-1]
     g = programs.heat3d(shape, T, bc, "f64", fuse=FUSED)
-    assert [l.get("deferred_scale") is not None for l in g.plan()["launches"]] == [True] * T
+    assert ["deferred_scales" in l for l in g.plan()["launches"]] == [True] * T
     got = to_host(g.run([to_dev(u0)])[0])
     assert np.isfinite(got).all()
     assert_close(got, ref, 1e-12, float(np.max(np.abs(u0))), "deferred weight, 1e280 %s" % bc)
@@ -315,6 +315,34 @@ def test_heat3d_deferred_weight_chunks_magnitudes_nan(bc):
     assert np.array_equal(np.isnan(got), np.isnan(ref))
     ok = ~np.isnan(ref)
     assert_close(got[ok], ref[ok], 1e-12, 1.0, "deferred weight with NaN %s" % bc)
+
+
+@pytest.mark.parametrize("bc", ["zero", "periodic"])
+def test_jacobi2d_deferred_weight_forms_magnitudes_nan(bc):
+    """30 steps of the 5-point average run as chunks of 13, 13 and 4 on ratio
+    1 (4 adds per cell), 0.2^m applied at each chunk's end, in every kernel
+    form and time-tile depth: the same bits in all of them, within the f64
+    tolerance of the oracle on inputs near 1e290, and NaN over the same
+    dependence cone."""
+    T = 30
+    shape = (37, 150)
+    u0 = inputs.uniform(shape, -1.0, 1.0, 21) * 1e290
+    u0[5, 70] = np.nan
+    ref = oracle.run(OP.jacobi2d(shape, T, bc), [u0])[-1]
+    assert 0 < np.isnan(ref).sum() < ref.size
+    res = []
+    for kernel, depth in ((0, 1), (0, 4), (1, 1), (1, 5), (1, 13)):
+        g = programs.jacobi2d(shape, T, bc, "f64")
+        g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+        g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+        g.fuse(FUSED)
+        got = to_host(g.run([to_dev(u0)])[0])
+        res.append(got.tobytes())
+    assert all(r == res[0] for r in res)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.isfinite(got[ok]).all()
+    assert_close(got[ok], ref[ok], 1e-12, 1e290, "deferred weight 2-D %s" % bc)
 
 
 def test_radius2_3d_stencil_paired_cells():

@@ -1035,8 +1035,11 @@ std::string describe_plan(const GraphImpl& g) {
          << ", \"regs\": " << ls.regs << ", \"occupancy\": " << ls.occupancy;
       if (!ls.code.defer_scales.empty()) {
         os << ", \"deferred_scales\": [";
-        for (size_t i = 0; i < ls.code.defer_scales.size(); ++i)
-          os << (i ? ", " : "") << ls.code.defer_scales[i];
+        for (size_t i = 0; i < ls.code.defer_scales.size(); ++i) {
+          char num[32];
+          std::snprintf(num, sizeof num, "%.17g", ls.code.defer_scales[i]);
+          os << (i ? ", " : "") << num;
+        }
         os << "]";
       }
       os << "}";

@@ -368,6 +368,21 @@ def test_plan_deferred_common_weight():
     g.output(g.stencil(x, programs.SEVEN_POINT, [0.3] + [0.7 / 6] * 6, "zero", 4))
     g.fuse(C.DCP_FUSE_ALL)
     assert all(s is None for s in scales(g))
+    # negative weights: f = -0.125 (the most frequent), ratios -4 and 1
+    g = Graph()
+    x = g.input("f64", (30, 40))
+    g.output(g.stencil(x, programs.FIVE_POINT, [0.5, -0.125, -0.125, -0.125, -0.125], "periodic", 5))
+    g.fuse(C.DCP_FUSE_ALL)
+    assert scales(g) == [1.0] * 4 + [pytest.approx((-0.125) ** 5, rel=1e-15)]
+    # one point: the steps are copies and the factor w^T comes once; a factor
+    # that would underflow keeps the plain sum
+    for T, deferred in ((10, True), (2000, False)):
+        g = Graph()
+        x = g.input("f64", (30, 40))
+        g.output(g.stencil(x, [(0, 0)], [0.5], "zero", T))
+        g.fuse(C.DCP_FUSE_ALL)
+        sc = scales(g)
+        assert (sc[-1] == pytest.approx(0.5 ** T, rel=1e-15)) if deferred else all(v is None for v in sc)
     # a fused chain of equal one-step nodes is one run, like one five-step node
     g = Graph()
     v = g.input("f64", (8, 9, 10))

@@ -1,28 +1,42 @@
 #!/usr/bin/env python3
 """Benchmark of the fused executor on one batch of synthetic input per step.
 
-Default workload (the configuration the headline metric is quoted on): the
-fused map+reduce program y = exp(a*x + b) * sin(x) - 0.5*x*x with sum(y) and
-max|y| over x, a, b of 2**26 float32 elements drawn N(0, 1).  One step = one
-dcp_run of the fused program (one kernel).  Inputs (805 MB) exceed the 129 MB
-L2, so no flush is needed between steps.
+Default workload (the largest configuration that fits one GPU, at the
+paper's binary64 arithmetic): the 3-D 7-point heat step (centre 0.4, six
+neighbours 0.1) on a 512^3 float64 grid with periodic boundaries, 50 steps,
+input U[-1, 1) from seed 1003 -- the heat3d form of the paper's stencil
+benchmarks.  One step = one dcp_run of the fused program (50 stencil
+launches).  The grid (1.07 GB) exceeds the 129 MB L2, so no flush is needed
+between steps.
 
 Metric: effective HBM GB/s = algorithmic bytes per step / device time per
-step (algorithmic bytes = every input read once, every output written once).
-Also reported: the same program op-by-op (one kernel per NumPy statement,
-every temporary in device memory) and as torch eager ops (the CuPy analogue
-of the paper's GPU comparison), the oracle on the host cores (cpu_baseline),
-the end-to-end rate through dcp_run_host (host buffers, copies inside the
-timed region), the roofline of the dominant kernel and the SM clocks sampled
-during the timed region.
+step; for iterated stencils the per-step convention (every stencil step
+reads and writes the grid once: 2 * steps * cells * 8 bytes).  The roofline
+of the dominant kernel is reported against the bound that holds on GB300:
+the FP64 pipes for binary64 programs (the 13 flops of the 7-point step as
+defined, over the FP64 rate measured in the same run by dcp_probe_fp64),
+with the FP64 issue fraction and the HBM fraction alongside; device memory
+for float32 programs.  Also reported: the same program op-by-op (one kernel
+per NumPy statement) and as torch eager ops (the CuPy analogue of the
+paper's GPU comparison), the oracle on the host cores (cpu_baseline: one
+thread, and the OpenMP build on every core), the end-to-end rate through
+dcp_run_host (host buffers, copies inside the timed region), and the SM
+clocks sampled during the timed region.
 
-Other workloads (--workload): map_reduce_f64, jacobi2d (256^2 f64, 10
-steps), heat3d (512^3 f64, 50 steps), batch2d (4096 instances f32, 20
-steps), tanh_adjoint (256^3 f64, 20 steps, steps/s of the reverse pass).
+Other workloads (--workload): map_reduce_f32 / map_reduce_f64 (2^26
+elements), map_reduce_rows_f32, jacobi2d (256^2 f64, 10 steps), batch2d
+(4096 instances f32, 20 steps), tanh_adjoint (256^3 f64, 20 steps, steps/s
+of the reverse pass).
 
-Multi-GPU (torchrun, one rank per GPU): each rank runs its own instance of
-the workload (weak scaling, no data-path collective); the time is the max
-over ranks and `value` aggregates all ranks.
+--impl reference times the oracle (the plain CPU interpreter the kernels are
+checked against) on the same workload and config, with the same bounded
+sample as the main line's cpu_baseline.
+
+Multi-GPU (torchrun, one rank per GPU): heat3d and map_reduce_* split ONE
+problem over the ranks (z-slabs with halo exchange; 1-D blocks with one
+exchange of partial results; strong scaling); the other workloads run one
+independent instance per rank (weak scaling, no data-path collective).  The
+time is the max over ranks and `value` is the whole job's rate.
 """
 from __future__ import annotations
 
@@ -53,17 +67,6 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
-
-
-def _ncu_traffic(kernel_name):
-    """DRAM bytes per launch recorded by an ncu capture of exactly this kernel
-    (profiles/*.md lines 'ncu-traffic: <kernel> <bytes>'); None otherwise."""
-    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
-        for line in open(path):
-            m = re.match(r"\s*ncu-traffic:\s+(\S+)\s+(\d+)", line)
-            if m and m.group(1) == kernel_name:
-                return int(m.group(2))
-    return None
 
 
 class ClockSampler:
@@ -146,6 +149,16 @@ class Workload:
         """Metric value for one step taking t_step seconds."""
         return self.bytes / t_step / GB
 
+    # -- the oracle on the host cores (cpu_baseline and the reference arm) --
+    # cpu_run() times one bounded sample of the workload through the oracle
+    # and returns its seconds; cpu_value(t) turns a sample time into the
+    # metric; cpu_scale is (one whole workload step) / (one sample), used to
+    # state the reference arm's ms_per_step; cpu_desc says what a sample is.
+    cpu_scale = 1.0
+
+    def cpu_value(self, t):
+        return self.value(t)
+
 
 def _np_dtype(d):
     import numpy as np
@@ -159,17 +172,15 @@ class MapReduce(Workload):
         self.name = "map_reduce_%s" % dtype
         self.bytes = 3 * n * (4 if dtype == "f32" else 8)
 
-    # FP64 operations per element of the f64 program as executed: exp and sin
-    # in binary64 have no fixed operation count, so the FP64 work is the one
-    # counted by ncu on the fused kernel (22 DFMA, 4 DADD, 5 DMUL per element
-    # with the kernels' own exp and sin, a DFMA counted as 2 flops)
-    F64_FLOPS_PER_ELEMENT = 53
-
     def roof(self):
-        # f32: device memory bound (3 arrays read once); f64: the FP64 pipes
+        # f32: device memory bound (3 arrays read once).  f64: bound by the
+        # FP64 pipes; exp and sin in binary64 have no algorithmic flop
+        # count, so the f64 line reports how busy the FP64 pipe is (the FP64
+        # instructions per element that ncu counted on this exact kernel,
+        # recorded in profiles/, over the probe's rate) and the HBM fraction
         if self.dtype == "f64":
-            return "alu", self.F64_FLOPS_PER_ELEMENT * self.n, "flop"
-        return "hbm", self.bytes, "bytes"
+            return {"bound": "alu_issue", "hbm_bytes": self.bytes, "elements": self.n}
+        return {"bound": "hbm", "bytes": self.bytes}
 
     def describe(self):
         return {"workload": "fused map+reduce: y = exp(a*x+b)*sin(x) - 0.5*x*x; sum(y), max|y|",
@@ -177,10 +188,14 @@ class MapReduce(Workload):
                 "l2": "inputs %.0f MB > 129 MB L2: no flush between steps" % (self.bytes / 1e6),
                 "algorithmic_bytes_per_step": self.bytes}
 
+    def host_setup(self):
+        from paper_2107_00555_gb300 import inputs
+        self.host = inputs.cfg2(_np_dtype(self.dtype), n=self.n)
+
     def setup(self, torch, dev):
         from paper_2107_00555_gb300 import _capi as C
-        from paper_2107_00555_gb300 import inputs, programs
-        self.host = inputs.cfg2(_np_dtype(self.dtype), n=self.n)
+        from paper_2107_00555_gb300 import programs
+        self.host_setup()
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         self.g = programs.map_reduce(self.n, self.dtype, fuse=C.DCP_FUSE_ALL)
         self.g0 = programs.map_reduce(self.n, self.dtype, fuse=0)
@@ -238,15 +253,15 @@ class MapReduce(Workload):
     def step_e2e_staged(self):
         self.call_staged()
 
-    def cpu_sample(self):
-        """Oracle on the full workload (2**26 elements), single thread."""
+    cpu_desc = "the full workload step: one oracle pass over all 2^26 elements"
+
+    def cpu_run(self):
         import oracle
         from oracle import programs as OP
         prog = OP.map_reduce(self.n)
         t0 = time.perf_counter()
         oracle.run(prog, list(self.host))
-        dt = time.perf_counter() - t0
-        return self.bytes / dt / GB, "full workload: 2^26 elements, one oracle pass", 1
+        return time.perf_counter() - t0
 
 
 class MapReduceRows(Workload):
@@ -262,7 +277,7 @@ class MapReduceRows(Workload):
         self.bytes = 3 * self.n * 4 + 2 * side * 4
 
     def roof(self):
-        return "hbm", self.bytes, "bytes"
+        return {"bound": "hbm", "bytes": self.bytes}
 
     def describe(self):
         return {"workload": "fused map + axis reduction: y = exp(a*x+b)*sin(x) - 0.5*x*x on "
@@ -271,11 +286,15 @@ class MapReduceRows(Workload):
                 "l2": "inputs %.0f MB > 129 MB L2: no flush between steps" % (3 * self.n * 4 / 1e6),
                 "algorithmic_bytes_per_step": self.bytes}
 
-    def setup(self, torch, dev):
+    def host_setup(self):
         import numpy as np
-        from paper_2107_00555_gb300 import _capi as C
-        from paper_2107_00555_gb300 import inputs, programs
+        from paper_2107_00555_gb300 import inputs
         self.host = [a.reshape(self.shape) for a in inputs.cfg2(np.float32, n=self.n)]
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import programs
+        self.host_setup()
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         self.g = programs.map_reduce(self.shape, "f32", fuse=C.DCP_FUSE_ALL, axis=1)
         self.g0 = programs.map_reduce(self.shape, "f32", fuse=0, axis=1)
@@ -316,17 +335,29 @@ class MapReduceRows(Workload):
     def step_e2e(self):
         self.call_host()
 
-    def cpu_sample(self):
-        """Oracle on the first 512 rows (1/16 of the workload), scaled per byte."""
+    @property
+    def cpu_rows(self):
+        return min(512, self.shape[0])
+
+    @property
+    def cpu_desc(self):
+        return "the first %d of the %d rows, scaled per byte" % (self.cpu_rows, self.shape[0])
+
+    @property
+    def cpu_scale(self):
+        return self.shape[0] / self.cpu_rows
+
+    def cpu_value(self, t):
+        return 3 * self.cpu_rows * self.shape[1] * 4 / t / GB
+
+    def cpu_run(self):
         import oracle
         from oracle import programs as OP
-        rows = min(512, self.shape[0])
-        sub = [a[:rows] for a in self.host]
-        prog = OP.map_reduce((rows, self.shape[1]), axis=1)
+        sub = [a[:self.cpu_rows] for a in self.host]
+        prog = OP.map_reduce((self.cpu_rows, self.shape[1]), axis=1)
         t0 = time.perf_counter()
         oracle.run(prog, sub)
-        dt = time.perf_counter() - t0
-        return 3 * rows * self.shape[1] * 4 / dt / GB, "first %d of %d rows" % (rows, self.shape[0]), 1
+        return time.perf_counter() - t0
 
 
 class Stencil(Workload):
@@ -348,32 +379,66 @@ class Stencil(Workload):
         self.size = 8
         self.bytes = 2 * self.T * self.cells * self.size
 
+    @property
+    def npts(self):
+        return 5 if self.name == "jacobi2d" else 7
+
     def roof(self):
-        # FP64 ALU bound: 5 (2-D) / 7 (3-D) weighted terms per cell and step,
-        # each a multiply and an add except the first (2k - 1 flops) -- the
-        # step as defined; with the deferred common weight the kernels
-        # execute k - 1 FP64 operations per cell and step
-        npts = 5 if self.name == "jacobi2d" else 7
+        # FP64 ALU bound.  Algorithmic work: the step as defined, p weighted
+        # terms per cell (a multiply and an add each, except the first add:
+        # 2p - 1 flops; 13 for the 7-point step).  Alongside: the FP64
+        # instructions the kernels execute per useful cell and step (p - 1
+        # on a deferred common weight, plus one multiply at chunk ends; p for
+        # the plain weighted sum), and the compulsory device-memory traffic
+        # of one launch (the grid read once and written once).
         steps_per_launch = self.T / max(1, self.n_launch)
-        return "alu", (2 * npts - 1) * self.cells * steps_per_launch, "flop"
+        return {"bound": "alu",
+                "flops": (2 * self.npts - 1) * self.cells * steps_per_launch,
+                "fp64_inst": self.fp64_inst_per_cell_step * self.cells * steps_per_launch,
+                "fp64_inst_per_cell_step": self.fp64_inst_per_cell_step,
+                "hbm_bytes": 2 * self.cells * self.size}
+
+    def plan_model(self, plan):
+        """FP64 instructions per useful cell and step, averaged over the run,
+        from the plan's per-step deferral factors."""
+        total, steps = 0.0, 0
+        for l in plan["launches"]:
+            lo, hi = l["steps"]
+            scales = l.get("deferred_scales")
+            for k in range(hi - lo):
+                if scales is None:
+                    total += self.npts          # one multiply + p - 1 FMAs
+                else:
+                    f = scales[k] if k < len(scales) else 1
+                    total += (self.npts - 1) + (0 if f == 1 else 1)
+                steps += 1
+        self.fp64_inst_per_cell_step = total / max(1, steps)
 
     def describe(self):
         form = ("2-D 5-point 0.2*(c+w+e+s+n)" if self.name == "jacobi2d"
-                else "3-D 7-point 0.4*c + 0.1*(6 neighbours)")
+                else "3-D 7-point 0.4*c + 0.1*(6 neighbours) (heat3d form)")
+        grid_mb = self.cells * self.size / 1e6
         return {"workload": "%s, %s, %s boundary, %d steps" % (form, "x".join(map(str, self.shape)),
                                                            self.bc, self.T),
-                "dtype": self.dtype, "algorithmic_bytes_per_step": self.bytes,
+                "dtype": self.dtype,
+                "inputs": ("U[0,1), seed 1001" if self.name == "jacobi2d" else "U[-1,1), seed 1003"),
+                "algorithmic_bytes_per_step": self.bytes,
                 "bytes_convention": "2 * steps * cells * 8 (each step reads and writes the grid)",
-                "l2": ("working set 1 MiB: L2-resident, launch-latency bound"
-                       if self.name == "jacobi2d" else "grid 1.07 GB > L2")}
+                "l2": ("working set %.1f MB: L2-resident, launch-latency bound" % (2 * grid_mb)
+                       if grid_mb * 2 < 129 else
+                       "grid %.0f MB > 129 MB L2: no flush between steps" % grid_mb)}
 
-    def setup(self, torch, dev):
-        from paper_2107_00555_gb300 import _capi as C
-        from paper_2107_00555_gb300 import inputs, programs
+    def host_setup(self):
+        from paper_2107_00555_gb300 import inputs
         if self.name == "jacobi2d":
             self.host = [inputs.cfg1(n=self.shape[0])]
         else:
             self.host = [inputs.cfg3(n=self.shape[0])]
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import programs
+        self.host_setup()
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         build = programs.jacobi2d if self.name == "jacobi2d" else programs.heat3d
         self.g = build(self.shape, self.T, self.bc, self.dtype)
@@ -389,9 +454,11 @@ class Stencil(Workload):
         # shorter than the Python-side checks of an unprepared call)
         self.call = self.g.prepare(self.dev, self.out)
         self.call0 = self.g0.prepare(self.dev, self.out0)
-        self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
+        plan = self.g.plan()
+        self.kernels = [l["kernel"] for l in plan["launches"]]
         self.n_launch = len(self.kernels)
         self.n_launch0 = self.g0.n_kernels
+        self.plan_model(plan)
 
     def step(self):
         self.call()
@@ -432,21 +499,41 @@ class Stencil(Workload):
     def step_e2e(self):
         self.call_host()
 
-    def cpu_sample(self):
+    # the oracle: the whole 2-D workload; for 3-D one of the steps on a slab
+    # of at most 64 planes with the full x-y extent (the same work per cell;
+    # periodic in the slab), scaled per cell
+    @property
+    def cpu_planes(self):
+        return self.shape[0] if len(self.shape) == 2 else min(64, self.shape[0])
+
+    @property
+    def cpu_desc(self):
+        if len(self.shape) == 2:
+            return "the full workload step (%s, %d steps)" % ("x".join(map(str, self.shape)), self.T)
+        return ("one of the %d steps on a %dx%dx%d slab (the full x-y extent; the same work per "
+                "cell), scaled per cell" % (self.T, self.cpu_planes, self.shape[1], self.shape[2]))
+
+    @property
+    def cpu_scale(self):
+        if len(self.shape) == 2:
+            return 1.0
+        return self.T * self.shape[0] / self.cpu_planes
+
+    def cpu_value(self, t):
+        return self.bytes / (t * self.cpu_scale) / GB
+
+    def cpu_run(self):
         import oracle
         from oracle import programs as OP
-        if self.name == "jacobi2d":
+        if len(self.shape) == 2:
             prog = OP.jacobi2d(self.shape, self.T, self.bc)
-            t0 = time.perf_counter()
-            oracle.run(prog, self.host)
-            dt = time.perf_counter() - t0
-            return self.bytes / dt / GB, "full workload (256^2, 10 steps)", 1
-        # 3-D: 2 of the 50 steps on the full 512^3 grid, scaled per step
-        prog = OP.heat3d(self.shape, 2, self.bc)
+            u = self.host[0]
+        else:
+            u = self.host[0][:self.cpu_planes]
+            prog = OP.heat3d(u.shape, 1, self.bc)
         t0 = time.perf_counter()
-        oracle.run(prog, self.host)
-        dt = time.perf_counter() - t0
-        return 2 * 2 * self.cells * 8 / dt / GB, "2 of 50 steps on the full 512^3 grid", 1
+        oracle.run(prog, [u])
+        return time.perf_counter() - t0
 
 
 class Batch(Workload):
@@ -460,7 +547,7 @@ class Batch(Workload):
     def roof(self):
         # compulsory device-memory traffic of one launch: every instance read
         # and written once (the launch advances all instances `depth` steps)
-        return "hbm", 2 * self.cells * 4, "bytes"
+        return {"bound": "hbm", "bytes": 2 * self.cells * 4}
 
     def describe(self):
         return {"workload": "4096 independent 2-D 5-point instances (0.2 weights, zero boundary), "
@@ -469,13 +556,17 @@ class Batch(Workload):
                 "algorithmic_bytes_per_step": self.bytes,
                 "bytes_convention": "2 * steps * cells * 4 (each step reads and writes every grid)"}
 
-    def setup(self, torch, dev):
-        from paper_2107_00555_gb300 import _capi as C
-        from paper_2107_00555_gb300 import inputs, programs
+    def host_setup(self):
+        from paper_2107_00555_gb300 import inputs
         self.host = inputs.cfg4()
         self.sides = [a.shape[0] for a in self.host]
         self.cells = sum(a.size for a in self.host)
         self.bytes = 2 * self.T * self.cells * 4
+
+    def setup(self, torch, dev):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import programs
+        self.host_setup()
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         self.g = programs.batch2d(self.sides, self.T, "zero", "f32")
         self.g.set_option(C.DCP_OPT_USE_GRAPH, 1)
@@ -516,16 +607,26 @@ class Batch(Workload):
     def step_e2e(self):
         self.call_host()
 
-    def cpu_sample(self):
+    cpu_desc = "the first 64 of the 4096 instances, all 20 steps, scaled per cell"
+
+    @property
+    def cpu_cells(self):
+        return sum(a.size for a in self.host[:64])
+
+    @property
+    def cpu_scale(self):
+        return self.cells / self.cpu_cells
+
+    def cpu_value(self, t):
+        return 2 * self.T * self.cpu_cells * 4 / t / GB
+
+    def cpu_run(self):
         import oracle
         from oracle import programs as OP
-        sample = self.host[:64]
-        cells = sum(a.size for a in sample)
         t0 = time.perf_counter()
-        for a in sample:
+        for a in self.host[:64]:
             oracle.run(OP.jacobi2d(a.shape, self.T, "zero"), [a])
-        dt = time.perf_counter() - t0
-        return 2 * self.T * cells * 4 / dt / GB, "first 64 of 4096 instances, all 20 steps", 1
+        return time.perf_counter() - t0
 
 
 class Adjoint(Workload):
@@ -547,17 +648,21 @@ class Adjoint(Workload):
         # FP64 ALU bound; count the stencil arithmetic only (13 flops per cell per
         # forward step and per reverse step), tanh and its derivative excluded
         cells = self.shape[0] ** 3
-        return "alu", 13 * cells * 2 * self.T / max(1, self.n_launch), "flop"
+        return {"bound": "alu", "flops": 13 * cells * 2 * self.T / max(1, self.n_launch)}
 
     def describe(self):
         return {"workload": "reverse pass of u_{t+1} = tanh(S7 u_t), loss = sum(u_T^2); 256^3 f64, "
                             "20 steps, periodic; forward tape + 20 reverse steps per call",
                 "dtype": "f64", "tape": "full (20 states, 2.7 GB)"}
 
+    def host_setup(self):
+        from paper_2107_00555_gb300 import inputs
+        self.host = [inputs.cfg5(n=self.shape[0])]
+
     def setup(self, torch, dev):
         from paper_2107_00555_gb300 import _capi as C
-        from paper_2107_00555_gb300 import inputs, programs
-        self.host = [inputs.cfg5(n=self.shape[0])]
+        from paper_2107_00555_gb300 import programs
+        self.host_setup()
         self.dev = [torch.from_numpy(a).to(dev) for a in self.host]
         self.prog = programs.tanh_chain(self.shape, self.T, fuse=C.DCP_FUSE_ALL)
         self.ones = [torch.ones((), dtype=torch.float64, device=dev)]
@@ -592,17 +697,23 @@ class Adjoint(Workload):
         self.prog.adjoint(self.dev, self.ones, self.grad)
         self.g_host.copy_(self.grad[0], non_blocking=True)
 
-    def cpu_sample(self):
+    cpu_desc = "a 64^3 sub-grid, all 20 steps forward and reverse, scaled per cell"
+
+    @property
+    def cpu_scale(self):
+        return self.shape[0] ** 3 / 64 ** 3
+
+    def cpu_value(self, t):
+        return self.T / (t * self.cpu_scale)
+
+    def cpu_run(self):
         import oracle
         from oracle import programs as OP
-        shape = (64, 64, 64)
-        prog = OP.tanh_chain(shape, self.T)
+        prog = OP.tanh_chain((64, 64, 64), self.T)
         u = self.host[0][:64, :64, :64].copy()
         t0 = time.perf_counter()
         oracle.adjoint(prog, [u], [1.0])
-        dt = time.perf_counter() - t0
-        scale = 64 ** 3 / 256 ** 3
-        return self.T / dt * scale, "64^3 sub-grid, 20 steps, scaled by cells to 256^3", 1
+        return time.perf_counter() - t0
 
 
 def make_workload(name, n=None):
@@ -669,13 +780,12 @@ def median_ci95(xs):
     return med, v[k - 1], v[n - k]
 
 
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 rate (DFMA counted as 2 flops)
-HBM_NOMINAL_GBS = 8000.0   # nominal GB300 HBM3e bandwidth
+FP64_NOMINAL_GFLOPS = 1250.0  # nominal GB300 FP64 rate (a DFMA counted as 2 flops)
+HBM_NOMINAL_GBS = 8000.0      # nominal GB300 HBM3e bandwidth
 
 
 def reduce_max(value, dist=None, device=None):
-    """Largest `value` over all ranks.  Used for timing only: the workload
-    itself has no collective (every rank runs an independent instance)."""
+    """Largest `value` over all ranks (timing only)."""
     if dist is None:
         return float(value)
     import torch
@@ -689,22 +799,114 @@ def weak_scaling_value(per_rank_work, world, t_max):
     return world * per_rank_work / t_max
 
 
-def _roofline(wl, per_launch_s):
+def _profile_value(key, kernel_name):
+    """A per-kernel figure recorded from an ncu capture of exactly this kernel
+    (profiles/*.md lines '<key>: <kernel> <number>'); None otherwise, e.g.
+    once the kernel's source (and so its name) has changed."""
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            m = re.match(r"\s*%s:\s+(\S+)\s+([0-9.eE+]+)" % re.escape(key), line)
+            if m and m.group(1) == kernel_name:
+                return float(m.group(2))
+    return None
+
+
+def _ncu_traffic(kernel_name):
+    v = _profile_value("ncu-traffic", kernel_name)
+    return int(v) if v is not None else None
+
+
+def measure_fp64_peak(stream):
+    """FP64 rate of this GPU, measured now by the library's probe (every SM
+    running independent DFMA chains; best of three launches)."""
+    from paper_2107_00555_gb300 import _capi as C
+    best = 0.0
+    for _ in range(3):
+        g, _ms = C.dcp_probe_fp64(0, 8192, stream.cuda_stream)
+        best = max(best, g)
+    return {"dfma_ginst_s": round(best, 2), "gflops": round(2 * best, 2),
+            "how": "dcp_probe_fp64: full-occupancy CTAs on every SM, 8 independent DFMA "
+                   "chains per thread, CUDA events; a DFMA = 2 flops; best of 3"}
+
+
+def _roofline(wl, per_launch_s, fp64):
     """Roofline of the dominant kernel from its algorithmic work per launch."""
-    bound, work, unit = wl.roof()
-    if bound == "hbm":
-        peak, src = _peaks()
-        achieved = work / per_launch_s / GB
-        return {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(wl.kernels[0]),
-                "kernel": wl.kernels[0], "peak_source": src,
+    r = wl.roof()
+    kernel = wl.kernels[0] if wl.kernels else None
+    hbm_peak, src = _peaks()
+    if r["bound"] == "hbm":
+        achieved = r["bytes"] / per_launch_s / GB
+        return {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": _ncu_traffic(kernel),
+                "kernel": kernel, "peak_source": src,
                 "frac_of_nominal": round(achieved / HBM_NOMINAL_GBS, 4)}
-    achieved = work / per_launch_s / 1e9
-    return {"bound": "alu", "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
-            "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-            "traffic": _ncu_traffic(wl.kernels[0]) if wl.kernels else None,
-            "kernel": wl.kernels[0] if wl.kernels else None,
-            "peak_source": "nominal FP64 1.25 TFLOP/s (probe measured 1.20)"}
+    out = {}
+    if r["bound"] == "alu":
+        achieved = r["flops"] / per_launch_s / 1e9
+        out = {"bound": "alu", "achieved": round(achieved, 2), "peak": fp64["gflops"],
+               "unit": "GFLOP/s", "frac": round(achieved / fp64["gflops"], 4),
+               "traffic": _ncu_traffic(kernel), "kernel": kernel,
+               "peak_source": "measured in this run (dcp_probe_fp64, DFMA rate x 2)",
+               "frac_of_nominal": round(achieved / FP64_NOMINAL_GFLOPS, 4),
+               "work": "algorithmic flops of the step as defined (2p - 1 per cell and step)"}
+        if "fp64_inst" in r:
+            ach_i = r["fp64_inst"] / per_launch_s / 1e9
+            out["fp64_issue"] = {
+                "inst_per_cell_step": round(r["fp64_inst_per_cell_step"], 4),
+                "achieved_ginst_s": round(ach_i, 2), "peak_ginst_s": fp64["dfma_ginst_s"],
+                "frac": round(ach_i / fp64["dfma_ginst_s"], 4),
+                "note": "FP64 instructions per useful cell and step executed by the kernels"}
+    else:  # FP64-bound without an algorithmic flop count (binary64 exp, sin)
+        per_el = _profile_value("ncu-fp64-inst-per-element", kernel)
+        out = {"bound": "alu", "unit": "G FP64 inst/s", "kernel": kernel,
+               "traffic": _ncu_traffic(kernel), "peak": fp64["dfma_ginst_s"],
+               "peak_source": "measured in this run (dcp_probe_fp64, DFMA lane rate)",
+               "work": "FP64 instructions per element counted by ncu on this kernel "
+                       "(issue fraction of the FP64 pipe; exp and sin have no flop count)"}
+        if per_el is not None:
+            ach_i = per_el * r["elements"] / per_launch_s / 1e9
+            out.update(achieved=round(ach_i, 2), frac=round(ach_i / fp64["dfma_ginst_s"], 4),
+                       fp64_inst_per_element=per_el)
+        else:
+            out.update(achieved=None, frac=None, fp64_inst_per_element=None)
+    if "hbm_bytes" in r:
+        ach_b = r["hbm_bytes"] / per_launch_s / GB
+        out["hbm"] = {"bytes_per_launch": r["hbm_bytes"], "achieved_gbs": round(ach_b, 2),
+                      "peak_gbs": hbm_peak, "frac": round(ach_b / hbm_peak, 4),
+                      "peak_source": src}
+    return out
+
+
+def _parallelism(wl, world):
+    if world <= 1:
+        return "single GPU"
+    if getattr(wl, "shardable", False):
+        return wl.shard_desc(world)
+    return "replicas: one independent workload per GPU"
+
+
+def _config(wl, world):
+    return dict(wl.describe(), parallelism=_parallelism(wl, world))
+
+
+def cpu_baseline(wl, runs=3, all_cores=False):
+    """The oracle, as it stands, on the host cores: the median of `runs`
+    bounded samples (wl.cpu_run), in the workload's metric."""
+    import oracle
+    if all_cores:
+        with oracle.all_cores() as ac:
+            if not ac.available:
+                return None
+            wl.cpu_run()  # first call loads the OpenMP build
+            t = statistics.median(wl.cpu_run() for _ in range(runs))
+            cores = ac.threads
+        kind = "oracle, OpenMP build (maps and stencil steps on every core; reductions and " \
+               "the transposed stencil sequential)"
+    else:
+        t = statistics.median(wl.cpu_run() for _ in range(runs))
+        cores, kind = 1, "oracle"
+    return {"value": round(wl.cpu_value(t), 6), "unit": wl.unit, "cores": cores, "kind": kind,
+            "sample": "%s; median of %d samples" % (wl.cpu_desc, runs)}
 
 
 def run_dcp(args):
@@ -719,7 +921,11 @@ def run_dcp(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     wl = make_workload(args.workload, args.n)
-    wl.setup(torch, dev)
+    sharded = world > 1 and getattr(wl, "shardable", False)
+    if sharded:
+        wl.setup_sharded(torch, dev, dist, rank, world)
+    else:
+        wl.setup(torch, dev)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -738,18 +944,25 @@ def run_dcp(args):
         plan = wl.g.plan()
         wl.kernels = [l["kernel"] for l in plan["launches"]] or wl.kernels
         wl.n_launch = len(plan["launches"]) or wl.n_launch
+        if hasattr(wl, "plan_model"):
+            wl.plan_model(plan)
     if hasattr(wl, "prog"):
         # reverse pass: its kernels, the most frequent first
         names = [l["kernel"] for l in wl.prog.plan().get("adjoint", {}).get("launches", [])]
         if names:
             wl.kernels = sorted(set(names), key=lambda k: -names.count(k))
             wl.n_launch = len(names)
+    fp64 = measure_fp64_peak(stream)
+    barrier()
     with ClockSampler(local) as clk:
         t = _time_device(torch, wl.step, args.steps, stream)
         barrier()
     t = max_over_ranks(t)
     t_step = t / args.steps
-    value = weak_scaling_value(wl.value(t_step) * t_step, world, t_step)
+    if sharded:
+        value = wl.value(t_step)          # the whole problem's rate (strong scaling)
+    else:
+        value = weak_scaling_value(wl.value(t_step) * t_step, world, t_step)
 
     # per-step device times: the dominant kernel's average launch duration
     # inside a step, and the median with its 95 % interval
@@ -760,7 +973,8 @@ def run_dcp(args):
         if rank == 0:
             print(json.dumps({"quick": True, "workload": wl.name, "ms_per_step": t_step * 1e3,
                               "value": value, "per_launch_ms": per_launch * 1e3,
-                              "median_ms": med * 1e3, "kernels": wl.kernels}), flush=True)
+                              "median_ms": med * 1e3, "kernels": wl.kernels,
+                              "fp64_peak": fp64}), flush=True)
         if dist is not None:
             dist.destroy_process_group()
         return
@@ -768,25 +982,27 @@ def run_dcp(args):
     for name, fn, nk in wl.legs():
         k = max(3, min(args.steps // 2, 10))
         fn()
-        t_leg = _time_device(torch, fn, k, stream) / k
-        extra[name] = {"value": round(wl.value(t_leg), 3), "unit": wl.unit,
-                       "kernels_per_step": nk, "speedup_fused": round(t_leg / t_step, 3)}
+        t_leg = max_over_ranks(_time_device(torch, fn, k, stream) / k)
+        extra[name] = {"value": round(wl.value(t_leg) if sharded else world * wl.value(t_leg), 3),
+                       "unit": wl.unit, "kernels_per_step": nk,
+                       "speedup_fused": round(t_leg / t_step, 3)}
     e2e = None
     wl.setup_e2e(torch) if hasattr(wl, "setup_e2e") else None
     if getattr(wl, "h2d", None):
         wl.step_e2e()
         k_e2e = max(3, min(args.steps, 10))
-        torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             wl.step_e2e()
         torch.cuda.synchronize()
         t_e2e = max_over_ranks((time.perf_counter() - t0) / k_e2e)
-        e2e = {"value": round(world * wl.value(t_e2e), 2), "unit": wl.unit,
-               "h2d_bytes_per_step": wl.h2d, "d2h_bytes_per_step": wl.d2h}
+        e2e = {"value": round(wl.value(t_e2e) if sharded else world * wl.value(t_e2e), 2),
+               "unit": wl.unit, "h2d_bytes_per_step": wl.h2d * (world if sharded else 1),
+               "d2h_bytes_per_step": wl.d2h * (world if sharded else 1)}
         if hasattr(wl, "step_e2e_staged"):
             wl.step_e2e_staged()
-            torch.cuda.synchronize()
+            barrier()
             t0 = time.perf_counter()
             for _ in range(k_e2e):
                 wl.step_e2e_staged()
@@ -800,7 +1016,8 @@ def run_dcp(args):
             dist.barrier()
             dist.destroy_process_group()
         return
-    cpu_value, cpu_sample, cores = wl.cpu_sample()
+    if not hasattr(wl, "host") or wl.host is None:
+        wl.host_setup()
     line = {
         "metric": wl.metric,
         "value": round(value, 3),
@@ -810,18 +1027,18 @@ def run_dcp(args):
         "warmup": args.warmup,
         "ms_per_step": round(t_step * 1e3, 5),
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None,
         "dtype": wl.dtype,
         "data": "synthetic",
-        "config": dict(wl.describe(), parallelism="replicas: one independent workload per GPU"
-                       if world > 1 else "single GPU"),
-        "roofline": _roofline(wl, per_launch),
-        "cpu_baseline": {"value": round(cpu_value, 6), "unit": wl.unit, "cores": cores,
-                         "kind": "oracle", "sample": cpu_sample},
+        "config": _config(wl, world),
+        "roofline": _roofline(wl, per_launch, fp64),
+        "cpu_baseline": cpu_baseline(wl),
+        "cpu_baseline_all_cores": cpu_baseline(wl, all_cores=True),
         "e2e": e2e,
         "gpu_launches": wl.n_launch * args.steps,
         "clocks": clk.summary(),
+        "fp64_peak_probe": fp64,
         "step_time_ms": {"median": round(med * 1e3, 5), "ci95": [round(lo * 1e3, 5), round(hi * 1e3, 5)],
                          "runs": len(times), "timed_separately": True},
     }
@@ -833,45 +1050,39 @@ def run_dcp(args):
 
 
 def run_reference(args):
-    """The oracle (plain CPU interpreter) as the reference arm, on the host cores."""
+    """The reference arm: the oracle (the plain CPU interpreter the kernels are
+    checked against), as it stands, single-threaded on the host cores, on the
+    same workload and config as the main line; every step is the workload's
+    bounded sample (the one its cpu_baseline times)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    import oracle
-    from oracle import programs as OP
-    from paper_2107_00555_gb300 import inputs
-    dtype = "f32" if args.workload.endswith("f32") else "f64"
-    n = 1 << 22  # bounded sample per step
-    host = inputs.cfg2(_np_dtype(dtype), n=n)
-    prog = OP.map_reduce(n)
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    wl = make_workload(args.workload, args.n)
+    wl.host_setup()
     for _ in range(args.warmup):
-        oracle.run(prog, list(host))
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.run(prog, list(host))
-    t = (time.perf_counter() - t0) / args.steps
-    bytes_ = 3 * n * (4 if dtype == "f32" else 8)
-    value = bytes_ / t / GB
-    sample = "2^22 of the 2^26 elements per step, single thread"
+        wl.cpu_run()
+    total = sum(wl.cpu_run() for _ in range(args.steps))
+    t = total / args.steps
+    value = wl.cpu_value(t)
     line = {
         "impl": "reference",
-        "metric": "Effective HBM GB/s",
-        "value": round(value, 4),
-        "unit": "GB/s",
-        "n_gpus": args.gpus,
+        "metric": wl.metric,
+        "value": round(value, 6),
+        "unit": wl.unit,
+        "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(t * 1e3, 3),
+        "ms_per_step": round(t * wl.cpu_scale * 1e3, 3),
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if world > 1 and getattr(wl, "shardable", False) else "weak",
         "vs_baseline": None,
-        "dtype": dtype,
+        "dtype": wl.dtype,
         "data": "synthetic",
-        "config": MapReduce(dtype).describe(),
-        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+        "config": _config(wl, world),
+        "cpu_baseline": {"value": round(value, 6), "unit": wl.unit, "cores": 1, "kind": "oracle",
+                         "sample": "%s; one sample per timed step" % wl.cpu_desc},
+        "e2e": {"value": round(value, 6), "unit": wl.unit, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -883,7 +1094,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dcp", choices=["dcp", "reference"])
-    ap.add_argument("--workload", default="map_reduce_f32")
+    ap.add_argument("--workload", default="heat3d")
     ap.add_argument("--n", type=int, default=None, help="element count override (profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="time the fused program only (no comparison legs); for profiling")

@@ -69,52 +69,109 @@ REDS = {"sum": 0, "max": 1, "min": 2, "maxabs": 3}
 DTYPES = ("f32", "f64", "i32", "i64")
 
 
+_LIB_OMP = os.path.join(_HERE, "_build", "libdcp_oracle_omp.so")
+_lib_omp = None
+_use_omp = False
+
+
+def _compile(out, extra):
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call([
+        "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        "-shared", _SRC, "-o", tmp] + extra + ["-lm"])
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle's C loops with the host compiler (binary64 kept literal)."""
     with _lock:
-        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-            tmp = _LIB + ".tmp%d" % os.getpid()
-            subprocess.check_call([
-                "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                "-shared", _SRC, "-o", tmp, "-lm"])
-            os.replace(tmp, _LIB)
+            _compile(_LIB, [])
     return _LIB
+
+
+def build_all_cores(force: bool = False):
+    """The same C loops built with OpenMP, for timing the oracle on every host
+    core (maps and stencil steps run in parallel; each output element is the
+    same expression in the same order, so results are bitwise those of the
+    checker build).  Returns the library path, or None if the host compiler
+    has no OpenMP."""
+    with _lock:
+        if force or not os.path.exists(_LIB_OMP) or \
+                os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+            try:
+                _compile(_LIB_OMP, ["-fopenmp"])
+            except (subprocess.CalledProcessError, OSError):
+                return None
+    return _LIB_OMP
+
+
+class all_cores:
+    """Context manager: oracle calls inside it use the OpenMP build (timing only).
+    ``threads`` is the number of threads it uses (``OMP_NUM_THREADS`` if set,
+    else every core this process may run on)."""
+
+    def __init__(self):
+        self.threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
+        self.available = False
+
+    def __enter__(self):
+        global _lib_omp, _use_omp
+        if _lib_omp is None:
+            path = build_all_cores()
+            if path is None:
+                return self
+            os.environ.setdefault("OMP_NUM_THREADS", str(self.threads))
+            _lib_omp = _declare(ctypes.CDLL(path))
+        _use_omp = True
+        self.available = True
+        return self
+
+    def __exit__(self, *exc):
+        global _use_omp
+        _use_omp = False
 
 
 def _load():
     global _lib
+    if _use_omp and _lib_omp is not None:
+        return _lib_omp
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        P = ctypes.c_void_p
-        I64 = ctypes.c_int64
-        I = ctypes.c_int
-        D = ctypes.c_double
-        lib.orc_map_f.argtypes = [I, I64, P, P, D, P]
-        lib.orc_map_i.argtypes = [I, I, I64, P, P, I64, P]
-        lib.orc_stencil_f.argtypes = [I, P, P, P, I, P, P, I, I]
-        lib.orc_stencil_vjp_f.argtypes = [I, P, P, P, I, P, P, I, I]
-        lib.orc_stencil_point_f.argtypes = [I, P, P, I, P, P, I, I, P, P]
-        lib.orc_stencil_point_f.restype = D
-        lib.orc_sum_seq.argtypes = [I64, P]
-        lib.orc_sum_seq.restype = D
-        lib.orc_sum_abs.argtypes = [I64, P]
-        lib.orc_sum_abs.restype = D
-        lib.orc_fsum.argtypes = [I64, P, P]
-        lib.orc_fsum.restype = D
-        lib.orc_reduce_ext_f.argtypes = [I, I64, P, P, P]
-        lib.orc_reduce_i.argtypes = [I, I, I64, P, P]
-        lib.orc_reduce_axis_f.argtypes = [I, I64, I64, I64, P, P, P, P]
-        lib.orc_reduce_axis_i.argtypes = [I, I, I64, I64, I64, P, P]
-        lib.orc_map_vjp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
-        lib.orc_map_jvp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
-        for f in (lib.orc_map_f, lib.orc_map_i, lib.orc_stencil_f, lib.orc_stencil_vjp_f,
-                  lib.orc_reduce_ext_f, lib.orc_reduce_i, lib.orc_map_vjp_f, lib.orc_map_jvp_f,
-                  lib.orc_reduce_axis_f, lib.orc_reduce_axis_i):
-            f.restype = I
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(_LIB))
     return _lib
+
+
+def _declare(lib):
+    """Argument and result types of the C entry points."""
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    I = ctypes.c_int
+    D = ctypes.c_double
+    lib.orc_map_f.argtypes = [I, I64, P, P, D, P]
+    lib.orc_map_i.argtypes = [I, I, I64, P, P, I64, P]
+    lib.orc_stencil_f.argtypes = [I, P, P, P, I, P, P, I, I]
+    lib.orc_stencil_vjp_f.argtypes = [I, P, P, P, I, P, P, I, I]
+    lib.orc_stencil_point_f.argtypes = [I, P, P, I, P, P, I, I, P, P]
+    lib.orc_stencil_point_f.restype = D
+    lib.orc_sum_seq.argtypes = [I64, P]
+    lib.orc_sum_seq.restype = D
+    lib.orc_sum_abs.argtypes = [I64, P]
+    lib.orc_sum_abs.restype = D
+    lib.orc_fsum.argtypes = [I64, P, P]
+    lib.orc_fsum.restype = D
+    lib.orc_reduce_ext_f.argtypes = [I, I64, P, P, P]
+    lib.orc_reduce_i.argtypes = [I, I, I64, P, P]
+    lib.orc_reduce_axis_f.argtypes = [I, I64, I64, I64, P, P, P, P]
+    lib.orc_reduce_axis_i.argtypes = [I, I, I64, I64, I64, P, P]
+    lib.orc_map_vjp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
+    lib.orc_map_jvp_f.argtypes = [I, I64, P, P, D, P, P, P, P]
+    for f in (lib.orc_map_f, lib.orc_map_i, lib.orc_stencil_f, lib.orc_stencil_vjp_f,
+              lib.orc_reduce_ext_f, lib.orc_reduce_i, lib.orc_map_vjp_f, lib.orc_map_jvp_f,
+              lib.orc_reduce_axis_f, lib.orc_reduce_axis_i):
+        f.restype = I
+    return lib
 
 
 def _p(a):

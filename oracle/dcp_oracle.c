@@ -15,11 +15,27 @@
  * -ffp-contract=off, no -ffast-math (no fused multiply-add, no
  * reassociation), so every sum below is evaluated exactly in the order
  * written.
+ *
+ * ORC_PARFOR / ORC_PARFOR2 mark the loops whose iterations write disjoint outputs (the
+ * elementwise maps and the stencil step).  The checker build ignores it.  A
+ * second build with -fopenmp, used only to time the oracle on every host
+ * core, runs those loops in parallel; every output element is still the
+ * same expression evaluated in the same order, so both builds give the
+ * same bits.  Reductions and the transposed (scatter) step stay
+ * sequential in both.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#define ORC_PARFOR _Pragma("omp parallel for schedule(static)")
+#define ORC_PARFOR2 _Pragma("omp parallel for collapse(2) schedule(static)")
+#else
+#define ORC_PARFOR
+#define ORC_PARFOR2
+#endif
 
 /* ---- operation codes (the oracle's own numbering) ---------------------- */
 enum {
@@ -49,24 +65,24 @@ static double orc_fmin_nan(double a, double b) {
 int orc_map_f(int op, int64_t n, const double* a, const double* b, double imm, double* y) {
   int64_t i;
   switch (op) {
-    case ORC_NEG:    for (i = 0; i < n; ++i) y[i] = -a[i]; break;
-    case ORC_ABS:    for (i = 0; i < n; ++i) y[i] = fabs(a[i]); break;
-    case ORC_EXP:    for (i = 0; i < n; ++i) y[i] = exp(a[i]); break;
-    case ORC_SIN:    for (i = 0; i < n; ++i) y[i] = sin(a[i]); break;
-    case ORC_COS:    for (i = 0; i < n; ++i) y[i] = cos(a[i]); break;
-    case ORC_TANH:   for (i = 0; i < n; ++i) y[i] = tanh(a[i]); break;
-    case ORC_SQRT:   for (i = 0; i < n; ++i) y[i] = sqrt(a[i]); break;
-    case ORC_SQUARE: for (i = 0; i < n; ++i) y[i] = a[i] * a[i]; break;
-    case ORC_ADD:    for (i = 0; i < n; ++i) y[i] = a[i] + b[i]; break;
-    case ORC_SUB:    for (i = 0; i < n; ++i) y[i] = a[i] - b[i]; break;
-    case ORC_MUL:    for (i = 0; i < n; ++i) y[i] = a[i] * b[i]; break;
-    case ORC_DIV:    for (i = 0; i < n; ++i) y[i] = a[i] / b[i]; break;
-    case ORC_MAX:    for (i = 0; i < n; ++i) y[i] = orc_fmax_nan(a[i], b[i]); break;
-    case ORC_MIN:    for (i = 0; i < n; ++i) y[i] = orc_fmin_nan(a[i], b[i]); break;
-    case ORC_ADD_S:  for (i = 0; i < n; ++i) y[i] = a[i] + imm; break;
-    case ORC_MUL_S:  for (i = 0; i < n; ++i) y[i] = a[i] * imm; break;
-    case ORC_SUB_S:  for (i = 0; i < n; ++i) y[i] = a[i] - imm; break;
-    case ORC_RSUB_S: for (i = 0; i < n; ++i) y[i] = imm - a[i]; break;
+    case ORC_NEG:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = -a[i]; } break;
+    case ORC_ABS:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = fabs(a[i]); } break;
+    case ORC_EXP:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = exp(a[i]); } break;
+    case ORC_SIN:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = sin(a[i]); } break;
+    case ORC_COS:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = cos(a[i]); } break;
+    case ORC_TANH:   { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = tanh(a[i]); } break;
+    case ORC_SQRT:   { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = sqrt(a[i]); } break;
+    case ORC_SQUARE: { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] * a[i]; } break;
+    case ORC_ADD:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] + b[i]; } break;
+    case ORC_SUB:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] - b[i]; } break;
+    case ORC_MUL:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] * b[i]; } break;
+    case ORC_DIV:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] / b[i]; } break;
+    case ORC_MAX:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = orc_fmax_nan(a[i], b[i]); } break;
+    case ORC_MIN:    { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = orc_fmin_nan(a[i], b[i]); } break;
+    case ORC_ADD_S:  { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] + imm; } break;
+    case ORC_MUL_S:  { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] * imm; } break;
+    case ORC_SUB_S:  { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = a[i] - imm; } break;
+    case ORC_RSUB_S: { ORC_PARFOR for (i = 0; i < n; ++i) y[i] = imm - a[i]; } break;
     default: return -1;
   }
   return 0;
@@ -189,18 +205,17 @@ static int orc_in_ring(const orc_st* s, int64_t z, int64_t y, int64_t x) {
 }
 
 static void orc_stencil_step(const orc_st* s, const double* in, double* out) {
-  int64_t z, y, x;
-  int k;
-  for (z = 0; z < s->n[0]; ++z)
-    for (y = 0; y < s->n[1]; ++y)
-      for (x = 0; x < s->n[2]; ++x) {
+  ORC_PARFOR2
+  for (int64_t z = 0; z < s->n[0]; ++z)
+    for (int64_t y = 0; y < s->n[1]; ++y)
+      for (int64_t x = 0; x < s->n[2]; ++x) {
         int64_t p = (z * s->n[1] + y) * s->n[2] + x;
         if (s->bc == ORC_BC_FIXED_RING && orc_in_ring(s, z, y, x)) {
           out[p] = in[p];
           continue;
         }
         double acc = 0.0;
-        for (k = 0; k < s->npts; ++k)
+        for (int k = 0; k < s->npts; ++k)
           acc += s->w[k] * orc_read(s, in, z + s->off[k * 3], y + s->off[k * 3 + 1],
                                     x + s->off[k * 3 + 2]);
         out[p] = acc;

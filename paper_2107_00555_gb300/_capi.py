@@ -98,6 +98,9 @@ _SIG = [
                                        ctypes.POINTER(ctypes.c_size_t)]),
     ("dcp_reduce_noalloc", ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                             _P, _P]),
+    ("dcp_probe_fp64", ctypes.c_int32, [ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), _P]),
     ("dcp_last_error", ctypes.c_char_p, []),
     ("dcp_version", ctypes.c_char_p, []),
 ]
@@ -227,6 +230,14 @@ def dcp_plan_info(g):
 def dcp_reduce_noalloc(in_ptr, n, dtype, red, out_ptr, stream=0):
     _check("dcp_reduce_noalloc", load().dcp_reduce_noalloc(in_ptr, int(n), dtype, red, out_ptr,
                                                            stream))
+
+
+def dcp_probe_fp64(op=0, iters=8192, stream=0):
+    """Returns (10^9 FP64 lane operations per second, milliseconds) of the probe."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _check("dcp_probe_fp64", load().dcp_probe_fp64(int(op), int(iters), ctypes.byref(g),
+                                                   ctypes.byref(ms), stream))
+    return g.value, ms.value
 
 
 def dcp_last_error():

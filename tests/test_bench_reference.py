@@ -1,0 +1,42 @@
+"""bench.py's reference arm (the oracle on the host cores) reports the same
+workload and config as the main line, so the two lines compare like with
+like; its value comes from the same bounded sample the main line's
+cpu_baseline times."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_config_matches_main_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "jacobi2d", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    wl = bench.make_workload("jacobi2d")
+    wl.host_setup()
+    assert line["config"] == json.loads(json.dumps(bench._config(wl, 1)))
+    assert line["metric"] == wl.metric and line["unit"] == wl.unit
+    assert line["cpu_baseline"]["value"] == line["value"] > 0
+
+
+def test_default_workload_is_the_largest_f64_configuration():
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert 'ap.add_argument("--workload", default="heat3d")' in src
+    wl = bench.make_workload("heat3d")
+    assert wl.shape == (512, 512, 512) and wl.T == 50 and wl.dtype == "f64"
+    assert wl.bc == "periodic"
+
+
+def test_every_workload_states_its_cpu_sample():
+    # batch2d's sample size depends on its drawn instance sides (host_setup)
+    for name in ("heat3d", "jacobi2d", "map_reduce_f32", "map_reduce_f64",
+                 "map_reduce_rows_f32", "tanh_adjoint"):
+        wl = bench.make_workload(name)
+        assert wl.cpu_desc and wl.cpu_scale >= 1.0

@@ -383,3 +383,20 @@ def test_graphs_on_concurrent_host_threads():
     assert not errors, errors
     for k in range(6):
         assert results[k] == serial[k], k
+
+
+@pytest.mark.gpu
+def test_fp64_probe_reports_a_plausible_rate():
+    """dcp_probe_fp64 (the FP64 roofline denominator): fused multiply-add, add
+    and multiply each give a positive lane rate, at most the FP32 rate of a
+    GB300 (152 SMs x 128 lanes x 2.07 GHz), and arguments are validated."""
+    torch.cuda.init()
+    s = torch.cuda.current_stream().cuda_stream
+    cap = 152 * 128 * 2.1
+    for op in (0, 1, 2):
+        g, ms = C.dcp_probe_fp64(op, 1024, s)
+        assert 0 < g < cap and ms > 0, (op, g, ms)
+    with pytest.raises(C.DcpError):
+        C.dcp_probe_fp64(3, 1024, s)
+    with pytest.raises(C.DcpError):
+        C.dcp_probe_fp64(0, 0, s)

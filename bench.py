@@ -250,6 +250,63 @@ class MapReduce(Workload):
         # page-locked host buffers: the fused kernel reads them directly
         self.call_host()
 
+    # -- one problem split over several GPUs (torchrun): 1-D blocks
+    shardable = True
+
+    def shard_desc(self, world):
+        from paper_2107_00555_gb300 import shard
+        return shard.ShardedMapReduce(self.n, world, 0, None, None).describe()
+
+    def setup_sharded(self, torch, dev, dist, rank, world):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import Graph, programs, shard
+        self.host_setup()
+        lo, hi = shard.block_range(self.n, world, rank)
+        self.dev = [torch.from_numpy(a[lo:hi].copy()).to(dev) for a in self.host]
+        self.g = programs.map_reduce(hi - lo, self.dtype, fuse=C.DCP_FUSE_ALL)
+        self.out = self.g.empty_outputs(dev)
+        call = self.g.prepare(self.dev, self.out)
+        combs = []
+        for red in ("sum", "maxabs"):
+            g = Graph()
+            t = g.input(self.dtype, (world,))
+            g.output(g.reduce(t, red))
+            g.fuse(C.DCP_FUSE_ALL)
+            combs.append(g)
+        self.combine_graphs = combs
+
+        def local_run(lo_, hi_):
+            return call()
+
+        def combine(j, table):
+            return combs[j].run([table.contiguous()])[0]
+
+        self.sm = shard.ShardedMapReduce(self.n, world, rank, local_run, combine, dist)
+        self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
+        self.n_launch = len(self.kernels) + 2
+        self.legs = lambda: []
+        self.step = self.sm.run
+        self.setup_e2e = self._setup_e2e_sharded
+        self.step_e2e = self._step_e2e_sharded
+
+    def _setup_e2e_sharded(self, torch):
+        # this rank's blocks from page-locked host memory, the results back
+        self.pin_in = []
+        for t in self.dev:
+            p = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+            p.copy_(t)
+            self.pin_in.append(p)
+        self.pin_out = [torch.empty((), dtype=self.dev[0].dtype, pin_memory=True) for _ in range(2)]
+        self.h2d = sum(p.numel() * p.element_size() for p in self.pin_in)
+        self.d2h = sum(p.element_size() for p in self.pin_out)
+
+    def _step_e2e_sharded(self):
+        for d, p in zip(self.dev, self.pin_in):
+            d.copy_(p, non_blocking=True)
+        res = self.sm.run()
+        for p, r in zip(self.pin_out, res):
+            p.copy_(r, non_blocking=True)
+
     def step_e2e_staged(self):
         self.call_staged()
 
@@ -391,12 +448,14 @@ class Stencil(Workload):
         # on a deferred common weight, plus one multiply at chunk ends; p for
         # the plain weighted sum), and the compulsory device-memory traffic
         # of one launch (the grid read once and written once).
+        # (a sharded rank's launches process its slab with halos)
+        cells = getattr(self, "roof_cells", self.cells)
         steps_per_launch = self.T / max(1, self.n_launch)
         return {"bound": "alu",
-                "flops": (2 * self.npts - 1) * self.cells * steps_per_launch,
-                "fp64_inst": self.fp64_inst_per_cell_step * self.cells * steps_per_launch,
+                "flops": (2 * self.npts - 1) * cells * steps_per_launch,
+                "fp64_inst": self.fp64_inst_per_cell_step * cells * steps_per_launch,
                 "fp64_inst_per_cell_step": self.fp64_inst_per_cell_step,
-                "hbm_bytes": 2 * self.cells * self.size}
+                "hbm_bytes": 2 * cells * self.size}
 
     def plan_model(self, plan):
         """FP64 instructions per useful cell and step, averaged over the run,
@@ -498,6 +557,76 @@ class Stencil(Workload):
 
     def step_e2e(self):
         self.call_host()
+
+    # -- one problem split over several GPUs (torchrun): z-slabs, halo exchange
+    @property
+    def shardable(self):
+        return self.name == "heat3d"
+
+    def shard_desc(self, world):
+        from paper_2107_00555_gb300 import programs, shard
+        plan = shard.SlabPlan(self.shape, 1, self.bc, self.T, world, 0, self.shard_depth)
+        return plan.describe()
+
+    shard_depth = int(os.environ.get("DCP_SHARD_DEPTH", "2"))
+
+    def setup_sharded(self, torch, dev, dist, rank, world):
+        from paper_2107_00555_gb300 import _capi as C
+        from paper_2107_00555_gb300 import programs, shard
+        self.host_setup()
+        offs = programs.SEVEN_POINT
+        plan = shard.SlabPlan(self.shape, shard.stencil_radius(offs), self.bc, self.T, world, rank,
+                              self.shard_depth)
+        self.plan_sh = plan
+        self.slab_host = plan.slab_of(self.host[0])
+        self.slab_dev = torch.from_numpy(self.slab_host.copy()).to(dev)
+        bufs = [torch.zeros(plan.local_shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        self.local_graphs, calls = {}, {}
+        for c in plan.chunks:
+            if c.steps in self.local_graphs:
+                continue
+            g = programs.heat3d(plan.local_shape, c.steps, self.bc, self.dtype)
+            g.fuse(C.DCP_FUSE_ALL)
+            self.local_graphs[c.steps] = g
+            for i in range(2):
+                calls[(c.steps, i)] = g.prepare([bufs[i]], [bufs[1 - i]])
+        handle = {id(bufs[0]): 0, id(bufs[1]): 1}
+
+        def advance(src, k, dst):
+            calls[(k, handle[id(src)])]()
+
+        it = iter(bufs)
+        self.ss = shard.ShardedStencil(plan, advance, lambda: next(it), dist, backend="nccl")
+        g0 = self.local_graphs[plan.chunks[0].steps]
+        plan0 = g0.plan()
+        self.kernels = [l["kernel"] for l in plan0["launches"]]
+        self.n_launch = sum(len(self.local_graphs[c.steps].plan()["launches"]) for c in plan.chunks)
+        self.plan_model({"launches": [l for c in plan.chunks
+                                      for l in self.local_graphs[c.steps].plan()["launches"]]})
+        self.roof_cells = 1
+        for d in plan.local_shape:
+            self.roof_cells *= d
+        self.legs = lambda: []
+        self.step = self._step_sharded
+        self.setup_e2e = self._setup_e2e_sharded
+        self.step_e2e = self._step_e2e_sharded
+
+    def _step_sharded(self):
+        self.ss.load(self.slab_dev)
+        return self.ss.run()
+
+    def _setup_e2e_sharded(self, torch):
+        # this rank's slab from page-locked host memory, its result back to it
+        self.pin_in = torch.empty(self.slab_dev.shape, dtype=torch.float64, pin_memory=True)
+        self.pin_in.copy_(torch.from_numpy(self.slab_host))
+        self.pin_out = torch.empty_like(self.pin_in, pin_memory=True)
+        self.h2d = self.pin_in.numel() * 8
+        self.d2h = self.pin_out.numel() * 8
+
+    def _step_e2e_sharded(self):
+        self.slab_dev.copy_(self.pin_in, non_blocking=True)
+        res = self._step_sharded()
+        self.pin_out.copy_(res, non_blocking=True)
 
     # the oracle: the whole 2-D workload; for 3-D one of the steps on a slab
     # of at most 64 planes with the full x-y extent (the same work per cell;
@@ -939,7 +1068,7 @@ def run_dcp(args):
     for _ in range(args.warmup):
         wl.step()
     barrier()
-    if hasattr(wl, "g"):
+    if hasattr(wl, "g") and not sharded:
         # the autotuner may have changed the plan during the warm-up runs
         plan = wl.g.plan()
         wl.kernels = [l["kernel"] for l in plan["launches"]] or wl.kernels
@@ -1088,6 +1217,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_probe(args):
+    """The FP64 rate of this GPU for each binary64 operation (the roofline
+    denominator of the f64 workloads), with the SM clocks sampled meanwhile."""
+    import torch
+    from paper_2107_00555_gb300 import _capi as C
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    C.dcp_probe_fp64(0, 8192, stream.cuda_stream)  # load the module, wake the clocks
+    res = {}
+    with ClockSampler(0) as clk:
+        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+            runs = [C.dcp_probe_fp64(op, 65536, stream.cuda_stream) for _ in range(5)]
+            res[name] = {"ginst_s": round(max(g for g, _ in runs), 2),
+                         "median_ginst_s": round(statistics.median(g for g, _ in runs), 2),
+                         "ms": round(statistics.median(m for _, m in runs), 3)}
+    props = torch.cuda.get_device_properties(0)
+    print(json.dumps({"probe": "fp64", "device": props.name, "sms": props.multi_processor_count,
+                      "ops": res, "gflops_dfma": round(2 * res["dfma"]["ginst_s"], 2),
+                      "clocks": clk.summary()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1098,10 +1248,14 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="element count override (profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="time the fused program only (no comparison legs); for profiling")
+    ap.add_argument("--probe", action="store_true",
+                    help="measure the FP64 rate (fma, add, mul) with clocks sampled, and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_dcp(args)

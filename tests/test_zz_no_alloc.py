@@ -6,11 +6,15 @@ out-of-memory error); it keeps its scratch in a fixed array inside the
 library.  It must agree with the ordinary graph path (input -> reduce ->
 output) within the reduction tolerance used everywhere else, on two calls
 in a row (the second call reuses the scratch the first one left behind).
+It is also checked against the oracle (the exactly rounded sum with the
+backward-stable bound, exact max / min, wrapped integer sums), and a
+warmed-up call must leave the device's free memory unchanged.
 This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2107_00555_gb300 import Graph, inputs
 from paper_2107_00555_gb300 import _capi as C
 
@@ -67,3 +71,47 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     C.dcp_reduce_noalloc(x.data_ptr(), 0, C.DCP_F32, C.DCP_SUM, out.data_ptr(), 0)
     torch.cuda.synchronize()
     assert float(out) == 0.0
+
+
+def _oracle_reduce(red, dtype, x):
+    if dtype.startswith("i"):
+        bits = 32 if dtype == "i32" else 64
+        return oracle.reduce_i(red, bits, x.astype(np.int64)), None
+    x64 = x.astype(np.float64)
+    if red == "sum":
+        return oracle.fsum(x64), oracle.sum_abs(x64)
+    return oracle.reduce_ext(red, x64)[0], None
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "i32", "i64"])
+@pytest.mark.parametrize("red", ["sum", "max", "min", "maxabs"])
+def test_noalloc_matches_oracle_and_allocates_nothing(dtype, red):
+    n = 2_500_003
+    x = _data(dtype, n)
+    if dtype.startswith("i"):
+        # sums that wrap: large magnitudes
+        x = (x.astype(np.int64) * (1 << (20 if dtype == "i32" else 52))).astype(x.dtype)
+    xd = to_dev(x)
+    out = torch.zeros((), dtype=xd.dtype, device=xd.device)
+    s = torch.cuda.current_stream().cuda_stream
+    ref, mag = _oracle_reduce(red, dtype, x)
+    # warm-up: the first call on a device looks up the scratch and loads the kernel
+    C.dcp_reduce_noalloc(xd.data_ptr(), n, CODES[dtype], REDS[red], out.data_ptr(), s)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    torch_bytes0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        out.fill_(7)
+        C.dcp_reduce_noalloc(xd.data_ptr(), n, CODES[dtype], REDS[red], out.data_ptr(), s)
+        torch.cuda.synchronize()
+        got = to_host(out).item()
+        if dtype.startswith("i"):
+            assert int(got) == int(ref), (got, ref)
+        elif red == "sum":
+            assert abs(float(got) - ref) <= red_tol_for(dtype) * mag, (got, ref)
+        else:
+            want = ref if dtype == "f64" else float(np.float32(ref))
+            assert float(got) == want, (got, want)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_allocated() == torch_bytes0

@@ -121,6 +121,17 @@ template <typename T> __device__ __forceinline__ T dcp_red_comb(int op, T a, T b
   if (op == 2) return (b < a || b != b) ? b : a;
   return (b > a || b != b) ? b : a;
 }
+// binary64 max|y|: both operands are magnitudes (sign bit clear), whose bit
+// patterns, read as unsigned integers, order like the values, with every NaN
+// above +inf, so the NaN-propagating maximum is an integer comparison and
+// spends nothing on the FP64 pipe (the bound of binary64 maps on GB300).
+template <> __device__ __forceinline__ double dcp_red_comb<double>(int op, double a, double b) {
+  if (op == 0) return dcp_add(a, b);
+  if (op == 3)
+    return (dcp_u64)__double_as_longlong(b) > (dcp_u64)__double_as_longlong(a) ? b : a;
+  if (op == 2) return (b < a || b != b) ? b : a;
+  return (b > a || b != b) ? b : a;
+}
 // Cross-block combine in the final type (wraps for integer sums).
 __device__ __forceinline__ double dcp_fin_comb(int op, double a, double b) {
   if (op == 0) return a + b;

@@ -258,15 +258,17 @@ dcp_status dcp_reduce_noalloc(const void* in, int64_t n, int32_t dtype, int32_t 
 /* Measurement helper (not a program operation; the paper measures on other
  * hardware): the FP64 arithmetic rate of the current device, the roofline
  * denominator of the binary64 kernels, whose FP64 pipes bound them on GB300.
- * Every SM runs full-occupancy CTAs whose threads advance eight independent
- * chains of one operation for `iters` iterations; the launch is timed with
- * CUDA events on `cuda_stream`, after one shorter warm-up launch.
+ * Every SM runs full-occupancy CTAs whose threads advance independent chains
+ * of one operation (each with its own operand registers) for about `iters`
+ * operations per thread and chain count; 4, 8 and 16 chains per thread are
+ * each timed with CUDA events on `cuda_stream` after a shorter warm-up
+ * launch, and the best rate is returned.
  *   op     0 = fused multiply-add, 1 = add, 2 = multiply (binary64)
  *   iters  1 .. 2^24 operations per chain (8192 runs for tens of ms on GB300)
  *   gops   receives 10^9 lane operations per second (a fused multiply-add
  *          counts once here; it is 2 flops)
- *   ms     (may be NULL) receives the timed launch's duration
- * Synchronous: waits for the timed launch.  Allocates nothing (a fixed
+ *   ms     (may be NULL) receives the best launch's duration
+ * Synchronous: waits for the timed launches.  Allocates nothing (a fixed
  * 64-byte sink inside the library keeps the arithmetic live). */
 dcp_status dcp_probe_fp64(int32_t op, int64_t iters, double* gops, double* ms, void* cuda_stream);
 

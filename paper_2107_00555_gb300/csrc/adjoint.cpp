@@ -465,11 +465,53 @@ void plan_adjoint(const GraphImpl& F, size_t budget, AdjointPlan& out) {
   }
   const int S = (int)stencils.size();
   const int K = (int)std::ceil(std::sqrt((double)S));
-  std::vector<int> bounds{0};
-  for (int i = K; i < S; i += K) bounds.push_back(stencils[i]);
-  bounds.push_back(N);
+  // A cut before stencil node stencils[i] keeps the forward values bitwise
+  // those of the unsegmented run when it falls on a chunk end of a deferred
+  // common-weight run: the run of equal one-input steps that the full-tape
+  // forward fuses is then split where it applies f^m anyway, so both halves
+  // round exactly like the whole.  Cuts move forward to the next such place
+  // (node boundaries between different chains always qualify).
+  auto chained = [&](int p, int q) {  // q's steps continue p's run
+    const Node& a = F.nodes[p];
+    const Node& b = F.nodes[q];
+    return b.in.size() == 1 && b.in[0] == p && P.users[p].size() == 1 && !P.is_out[p] &&
+           a.weights == b.weights && a.offsets == b.offsets && a.bc == b.bc &&
+           a.dtype == b.dtype && defer_chunk_steps(a) > 0;
+  };
+  auto aligned = [&](int i) {
+    if (!chained(stencils[i - 1], stencils[i])) return true;
+    const int D = defer_chunk_steps(F.nodes[stencils[i]]);
+    long long steps = 0;
+    int j = i - 1;
+    for (;;) {
+      steps += F.nodes[stencils[j]].steps;
+      if (j == 0 || !chained(stencils[j - 1], stencils[j])) break;
+      --j;
+    }
+    // an unbounded run applies f^L once at its end: no cut inside it is free
+    return D != INT32_MAX && steps % D == 0;
+  };
+  auto segment = [&](bool align) {
+    std::vector<int> bounds{0};
+    for (int i = K; i < S; i += K) {
+      if (align)
+        while (i < S && !aligned(i)) ++i;
+      if (i < S) bounds.push_back(stencils[i]);
+    }
+    bounds.push_back(N);
+    return bounds;
+  };
   AdjointPlan ch;
-  build(bounds, ch);
+  std::vector<int> bounds = segment(true);
+  if (bounds.size() > 2) {
+    build(bounds, ch);
+  }
+  if (bounds.size() <= 2 || ch.tape_bytes > budget) {
+    // no aligned cut fits the budget: cut every K stencil nodes (forward
+    // values may then differ from the full tape's in their last bits)
+    bounds = segment(false);
+    build(bounds, ch);
+  }
   ch.chunked = true;
   if (ch.tape_bytes > budget)
     fail(DCP_E_OOM, "even sqrt(T) checkpointing needs " + std::to_string(ch.tape_bytes) +

@@ -239,6 +239,10 @@ CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 CodegenOut gen_map_adjoint_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int step);
 
+// Steps per chunk of a deferred common-weight run of stencil node n's steps
+// (0: plain weighted sum; INT32_MAX: no growth bound).
+int defer_chunk_steps(const Node& n);
+
 uint64_t fnv1a(const std::string& s);
 
 constexpr int kMaxIO = 16;       // loads / stores / reductions per kernel

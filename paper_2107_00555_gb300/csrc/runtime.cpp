@@ -728,7 +728,7 @@ std::string group_signature(const GraphImpl& g, const Group& G, int device_sms) 
   return h;
 }
 
-std::vector<TuneCfg> tune_candidates(const Group& G) {
+std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
   std::vector<TuneCfg> c;
   const int S = (int)G.steps.size();
   const int nd = group_nd(G);
@@ -750,6 +750,21 @@ std::vector<TuneCfg> tune_candidates(const Group& G) {
   if (nd == 1) tiles = {{1, 256}, {1, 512}, {1, 1024}};
   else if (G.dtype == DCP_F32) tiles = {{32, 64}, {64, 64}, {16, 128}, {32, 128}, {64, 32}};
   else tiles = {{32, 32}, {16, 64}, {32, 64}, {64, 32}, {16, 32}, {16, 16}, {8, 32}};
+  // small binary64 grids are bound by the FP64 pipes of the SMs they occupy:
+  // tile shapes whose count is at most one or two per SM balance that work
+  // (e.g. 152 tiles of 14 x 32 on a 256 x 256 grid)
+  if (nd == 2 && G.kind != GroupKind::Batch && G.dtype == DCP_F64 && sms > 0) {
+    const int64_t ny = G.shape[0], nx = G.shape[1];
+    for (int per_sm : {1, 2})
+      for (int tx : {16, 32, 64}) {
+        const int64_t tiles_x = (nx + tx - 1) / tx;
+        const int64_t rows = (int64_t)per_sm * sms / tiles_x;
+        if (rows < 1) continue;
+        const int64_t ty = (ny + rows - 1) / rows;
+        if (ty >= 4 && ty <= 256 && tiles_x * ((ny + ty - 1) / ty) * 2 > (int64_t)per_sm * sms)
+          tiles.push_back({(int)ty, tx});
+      }
+  }
   for (int d : depths)
     for (const auto& t : tiles) {
       int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
@@ -843,7 +858,7 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
     TuneCfg best = {G.depth, G.variant == 1 ? -1 : G.tile[0], G.variant == 1 ? G.seg : G.tile[1],
                     G.variant == 1 ? G.prefetch : G.tile[2], G.cx};
     float best_ms = 1e30f;
-    for (const auto& cfg : tune_candidates(G)) {
+    for (const auto& cfg : tune_candidates(G, rt.sms)) {
       try {
         apply_config(g, gi, cfg);
       } catch (const Error&) {

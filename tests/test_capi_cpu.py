@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2107_00555_gb300 import DcpError, Graph, programs
@@ -328,9 +329,10 @@ def test_plan_deferred_common_weight():
     """Linear runs of f64 steps with weights f * r_k (r_k exact) run on the
     ratios and apply f^m at the end of every chunk of m <= D steps,
     (sum |r_k|)^D <= 2^32: D = 9 for the 7-point heat stencil (0.4 = 4 * 0.1,
-    sum of ratios 10), 13 for the 5-point average.  Fixed rings, single
-    steps, f32 and weights without exact ratios keep the plain weighted sum
-    (no "deferred_scales" in the launch)."""
+    sum of ratios 10), 13 for the 5-point average; f32 runs bound the growth
+    by 2^16 instead (D = 4 and 6) and round f^m once to f32.  Fixed rings,
+    single steps and weights without exact ratios keep the plain weighted
+    sum (no "deferred_scales" in the launch)."""
     def scales(g):
         out = []
         for l in g.plan()["launches"]:
@@ -358,11 +360,21 @@ def test_plan_deferred_common_weight():
                 assert s == pytest.approx(want, rel=1e-14), (kernel, depth, i, s)
     for g in (programs.heat3d((8, 9, 10), 5, "fixed_ring", "f64", fuse=C.DCP_FUSE_ALL),
               programs.heat3d((8, 9, 10), 1, "periodic", "f64", fuse=C.DCP_FUSE_ALL),
-              programs.heat3d((8, 9, 10), 5, "periodic", "f32", fuse=C.DCP_FUSE_ALL),
-              programs.jacobi2d((40, 50), 10, "zero", "f32", fuse=C.DCP_FUSE_ALL),
               programs.jacobi2d((40, 50), 10, "fixed_ring", "f64", fuse=C.DCP_FUSE_ALL),
               programs.tanh_chain((8, 9, 10), 3, fuse=C.DCP_FUSE_ALL)):
         assert all(s is None for s in scales(g))
+    # binary32: chunks bounded by 2^16, f^m from binary64 rounded once to f32
+    f1, f2 = float(np.float32(0.1)), float(np.float32(0.2))
+    sc = scales(programs.heat3d((8, 9, 10), 9, "periodic", "f32", fuse=C.DCP_FUSE_ALL))
+    assert sc == [1.0] * 3 + [float(np.float32(f1 ** 4))] + [1.0] * 3 + \
+        [float(np.float32(f1 ** 4)), f1]
+    for kernel in (0, 1):
+        g = programs.jacobi2d((40, 50), 20, "zero", "f32")
+        g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+        g.fuse(C.DCP_FUSE_ALL)
+        sc = scales(g)
+        assert [i for i, x in enumerate(sc) if x != 1.0] == [5, 11, 17, 19]
+        assert sc[5] == float(np.float32(f2 ** 6)) and sc[19] == float(np.float32(f2 ** 2))
     g = Graph()
     x = g.input("f64", (8, 9, 10))
     g.output(g.stencil(x, programs.SEVEN_POINT, [0.3] + [0.7 / 6] * 6, "zero", 4))

@@ -181,3 +181,39 @@ def test_plan_lists_the_reverse_pass_kernels():
     _adjoint(g, [u0], [np.array(1.0)], budget=5 * u0.nbytes)
     adj = g.plan()["adjoint"]
     assert adj["checkpointed"] and "recompute" in [l["phase"] for l in adj["launches"]]
+
+
+def _paired_tanh_chain(shape, T):
+    """u_{t+1} = tanh(S(S(u_t))), loss = sum(u_T^2): every pair of separate
+    one-step heat nodes is one deferred common-weight run of two steps."""
+    p = oracle.Program()
+    pv = p.input("f64", shape)
+    g = Graph()
+    gv = g.input("f64", shape)
+    for _ in range(T):
+        for _ in range(2):
+            pv = p.stencil(pv, OP.SEVEN, OP.W7, "periodic", 1)
+            gv = g.stencil(gv, programs.SEVEN_POINT, programs.SEVEN_WEIGHTS, "periodic", 1)
+        pv = p.map("tanh", [pv])
+        gv = g.map("tanh", [gv])
+    p.output(p.reduce(p.map("square", [pv]), "sum"))
+    g.output(g.reduce(g.map("square", [gv]), "sum"))
+    g.fuse(C.DCP_FUSE_ALL)
+    return p, g
+
+
+def test_checkpoint_cuts_do_not_split_a_deferred_run():
+    """Eight stencil nodes in four deferred runs of two: sqrt(8) checkpointing
+    would cut after the third node, inside a run, where the full-tape forward
+    applies no factor; the planner moves the cut to the run's end, so the
+    checkpointed gradient is bitwise the full tape's, and both match the
+    oracle's reverse pass."""
+    shape = (12, 14, 16)
+    u0 = inputs.uniform(shape, -1.0, 1.0, 25)
+    p, g = _paired_tanh_chain(shape, 4)
+    (ref,) = oracle.adjoint(p, [u0], [1.0])
+    (full,) = _adjoint(g, [u0], [np.array(1.0)])
+    (ck,) = _adjoint(g, [u0], [np.array(1.0)], budget=3 * u0.nbytes)
+    assert g.plan()["adjoint"]["checkpointed"] is True
+    assert full.tobytes() == ck.tobytes()
+    assert_close(full, ref, 1e-12, float(np.max(np.abs(ref))), "paired tanh chain adjoint")

@@ -121,7 +121,9 @@ enum {
   DCP_OPT_STREAM_PREFETCH = 11, /* warp-stream stencils: row windows requested ahead (1..4) */
   DCP_OPT_STREAM_THREADS = 12, /* warp-stream stencils: threads per CTA (32..1024, multiple of 32; default 64) */
   DCP_OPT_CELLS_PER_THREAD = 13, /* 3-D stencils: cells per thread along x (1 or 2) */
-  DCP_OPT_MAP_UNROLL = 14       /* map kernels: 16-byte vectors per array in flight per thread (1..8) */
+  DCP_OPT_MAP_UNROLL = 14,      /* map kernels: 16-byte vectors per array in flight per thread (1..8) */
+  DCP_OPT_DEFERRED_WEIGHT = 15  /* stencils: 1 (default) deferred common weight where it applies,
+                                   0 the plain weighted sum everywhere (set before dcp_fuse) */
 };
 
 /* ---- graph construction ------------------------------------------------ */
@@ -151,11 +153,17 @@ dcp_status dcp_add_map(dcp_graph g, int32_t op, int32_t n_in, const dcp_value* i
  * o_k = offsets[k*ndim .. k*ndim+ndim-1] (axis order as the shape, last
  * axis contiguous), boundary rule `bc`.  Floating dtypes, 1..3 axes,
  * 1 <= npoints <= 32, |offset| <= 4 per axis, steps >= 0.  Rounding: each
- * step is one multiply and FMAs in point order, except that a float64 run
- * of two or more steps with a zero or periodic boundary whose weights are
- * exact multiples of one weight f sums the exact ratios w_k / f and applies
- * f^m every m steps (m bounded so that the scaled state grows by at most
- * 2^32: finite results for inputs up to about 1e298). */
+ * step is one multiply and FMAs in point order, except on a deferred common
+ * weight: a run of two or more steps with a zero or periodic boundary,
+ * beginning at the first step of its fused group, whose weights are exact
+ * multiples of one weight f, sums the exact ratios w_k / f and applies f^m
+ * every m steps, m bounded so that the scaled state grows by at most 2^32
+ * (float64) or 2^16 (float32).  Such a run keeps finite results for inputs
+ * up to the type's largest value over that growth (about 1.8e299 for the
+ * heat step, 2.2e34 for a float32 five-point average); its first launch
+ * records the largest finite |input| it reads, and dcp_sync (or
+ * dcp_run_host) returns DCP_E_UNSUPPORTED when that exceeds the run's bound.
+ * DCP_OPT_DEFERRED_WEIGHT = 0 selects the plain weighted sum throughout. */
 dcp_status dcp_add_stencil(dcp_graph g, dcp_value in, int32_t npoints, const int32_t* offsets,
                            const double* weights, int32_t bc, int32_t steps, dcp_value* out);
 
@@ -204,10 +212,11 @@ dcp_status dcp_run(dcp_graph g, const void* const* inputs, void* const* outputs,
                    void* cuda_stream);
 
 /* As dcp_run, but inputs and outputs are HOST pointers, and the call waits
- * for the stream before returning.  When every buffer is page-locked
- * (cudaHostAlloc / cudaHostRegister) the kernels read and write the host
- * buffers directly; otherwise the inputs are copied to graph-owned device
- * staging buffers and the outputs copied back (DCP_OPT_HOST_ACCESS). */
+ * for the stream before returning (then reporting what dcp_sync reports).
+ * When every buffer is page-locked (cudaHostAlloc / cudaHostRegister) the
+ * kernels read and write the host buffers directly; otherwise the inputs are
+ * copied to graph-owned device staging buffers and the outputs copied back
+ * (DCP_OPT_HOST_ACCESS). */
 dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const* host_outputs,
                         void* cuda_stream);
 
@@ -223,7 +232,10 @@ dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const
 dcp_status dcp_run_adjoint(dcp_graph g, const void* const* inputs, const void* const* out_grads,
                            void* const* in_grads, size_t tape_budget_bytes, void* cuda_stream);
 
-/* Waits for `cuda_stream` and reports asynchronous CUDA errors. */
+/* Waits for `cuda_stream` and reports asynchronous CUDA errors, and
+ * DCP_E_UNSUPPORTED when a deferred common-weight run of the last dcp_run
+ * read an input above the magnitude it keeps finite (see dcp_add_stencil;
+ * reported once). */
 dcp_status dcp_sync(dcp_graph g, void* cuda_stream);
 
 /* Overrides a planner choice (DCP_OPT_*).  Allowed before dcp_fuse (tile and

@@ -3,6 +3,7 @@
 // specialised with the group's expression DAG, stencil weights, tile shape
 // and boundary rule.  The expression is emitted as straight-line code in
 // registers; constants are emitted bit-exactly.
+#include <cfloat>
 #include <cinttypes>
 #include <cstdint>
 #include <cmath>
@@ -308,6 +309,7 @@ struct Defer {
   std::vector<int> order;     // point order: a ratio-1 point first
   std::vector<double> ratio;  // r_k = w_k / f, exact
   double scale = 1.0;         // multiply after this step (1.0: none)
+  double max_input = 0.0;     // largest finite |input| the run keeps finite
 };
 
 bool defer_ratios(const std::vector<double>& w, std::vector<double>& ratio, double& f_out,
@@ -359,6 +361,8 @@ Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   const Node& n = g.nodes[G.steps[s].node];
   const bool f32 = n.dtype == DCP_F32;
   if ((n.dtype != DCP_F64 && !f32) || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return d;
+  auto opt = g.options.find(DCP_OPT_DEFERRED_WEIGHT);
+  if (opt != g.options.end() && opt->second == 0) return d;
   const int S = (int)G.steps.size();
   // steps of the group share their offsets; a run also needs the same
   // weights and boundary
@@ -371,7 +375,9 @@ Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   int b = s + 1;
   while (b < S && same(b) && G.steps[b - 1].epi.empty()) ++b;
   const int L = b - a;
-  if (L < 2) return d;
+  // a run begins at the group's first step, whose input the first launch
+  // reads and checks (the magnitude guard); later runs keep the plain sum
+  if (L < 2 || a != 0) return d;
   std::vector<double> r, w = n.weights;
   if (f32)
     for (double& x : w) x = (double)(float)x;  // the kernel's float32 weights
@@ -403,6 +409,10 @@ Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   for (int k = 0; k < (int)r.size(); ++k)
     if (k != d.order[0]) d.order.push_back(k);
   d.scale = m > 0 ? power(m) : 1.0;
+  // the scaled state of a chunk of D steps is at most (sum |r_k|)^D times the
+  // largest |input| (sum |r_k| <= 1: no growth)
+  const double growth = gsum <= 1.0 ? 1.0 : std::pow(gsum, (double)D);
+  d.max_input = (f32 ? (double)FLT_MAX : DBL_MAX) / growth;
   return d;
 }
 
@@ -458,6 +468,8 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
      << (last ? (int)G.reds.size() : 0) << "\n#define DCP_NSCALAR " << G.scalars.size() << "\n";
   os << "#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_NSTEPS " << nsteps
      << "\n#define DCP_PDM " << G.prefetch << "\n";
+  const Defer guard = first ? plan_defer(g, G, 0) : Defer();
+  os << "#define DCP_GUARD " << (guard.on ? 1 : 0) << "\n";
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   if (!batch) emit_stencil_io(os, g, G, first, last);
@@ -520,6 +532,7 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
   out.smem_bytes = 0;
   for (double x : scales)
     if (x != 0.0) out.defer_scales = scales;
+  out.guard_max_input = guard.on ? guard.max_input : 0.0;
   out.source = finish(batch ? "dcp_bstream" : "dcp_stream", os.str());
   out.name = kname_of(out.source);
   return out;
@@ -548,10 +561,13 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
   int nred = last ? (int)G.reds.size() : 0;
   os << "#define DCP_NSTORE " << nstore << "\n#define DCP_NRED " << nred << "\n#define DCP_NSCALAR "
      << G.scalars.size() << "\n";
+  const Defer guard = first ? plan_defer(g, G, 0) : Defer();
+  os << "#define DCP_GUARD " << (guard.on ? 1 : 0) << "\n";
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   CodegenOut out;
   out.threads = threads;
+  out.guard_max_input = guard.on ? guard.max_input : 0.0;
   if (nd <= 2) {
     const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
     const int RY = nd == 1 ? 0 : ry;

@@ -229,6 +229,9 @@ struct CodegenOut {
   // sums ratios to a deferred common weight (1: none), 0 for a plain sum;
   // empty when no step of the launch is deferred
   std::vector<double> defer_scales;
+  // first launch of a deferred run: the largest finite |input| that run keeps
+  // finite (its magnitude guard's bound); 0 when the launch has no guard
+  double guard_max_input = 0.0;
 };
 CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 // Stencil launch `chunk` covers steps [s0, s1) of the group.

@@ -241,6 +241,43 @@ template <typename T> struct DcpStParamsT {
   int seg, pad_;            // warp-stream kernels: rows per work item
   typename DcpFin<T>::type* partials;
   unsigned int* ticket;
+  unsigned long long* guard;  // first launch of a deferred run: largest |input| seen
+};
+
+// Bit pattern of an element type (column masks of the warp-stream kernels).
+template <typename T> struct DcpBits { typedef unsigned type; };
+template <> struct DcpBits<double> { typedef unsigned long long type; };
+__device__ __forceinline__ float dcp_keep(float v, unsigned m) {
+  return __uint_as_float(__float_as_uint(v) & m);
+}
+__device__ __forceinline__ double dcp_keep(double v, unsigned long long m) {
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(v) & m));
+}
+
+// Magnitude guard of a deferred common-weight run (DCP_GUARD kernels): the
+// largest finite |value| the first launch reads, as the bit pattern with the
+// sign cleared (such patterns order like the magnitudes).  Integer work only;
+// non-finite inputs are skipped (they propagate the same way in either sum).
+struct DcpGuard {
+  unsigned long long m;
+  __device__ __forceinline__ DcpGuard() : m(0ull) {}
+  __device__ __forceinline__ void see(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+    if (b < 0x7ff0000000000000ull && b > m) m = b;
+  }
+  __device__ __forceinline__ void see(float v) {
+    const unsigned long long b = __float_as_uint(v) & 0x7fffffffu;
+    if (b < 0x7f800000ull && b > m) m = b;
+  }
+  // one atomic per warp; every lane of the warp must call it
+  __device__ __forceinline__ void flush(unsigned long long* dst) {
+    unsigned long long v = m;
+    for (int o = 16; o >= 1; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(dst, v);
+  }
 };
 
 // Launch parameters of axis-reduction kernels (passed by value).  The

@@ -13,7 +13,7 @@
 // FIXED_RING -- ring cells keep their value.
 //
 // The generated prefix defines DCP_T, DCP_TX, DCP_TY, DCP_RX, DCP_RY,
-// DCP_NSTEPS, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST,
+// DCP_NSTEPS, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_GUARD,
 // DCP_NLOAD, DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED,
 // dcp_red_op(r) and the functions
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)  (prologue)
@@ -142,7 +142,12 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   for (int i = 0; i < DCP_NSCALAR; ++i) sc[i] = p.sc[i][0];
   const int ny = p.ny, nx = p.nx;
   const int tyi = blockIdx.x / p.tiles_x, txi = blockIdx.x - tyi * p.tiles_x;
-  dcp_tile(A, B, ny, nx, tyi, txi, [&](long long gi) { return dcp_input(p, sc, gi); });
+  DcpGuard guard;
+  dcp_tile(A, B, ny, nx, tyi, txi, [&](long long gi) {
+    const T v = dcp_input(p, sc, gi);
+    if (DCP_GUARD) guard.see(v);
+    return v;
+  });
 
   // Write the tile centre (last launch: post maps, stores and reductions).
   T acc[DCP_ARR(DCP_NRED)];
@@ -169,6 +174,9 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #if DCP_LAST && DCP_NRED > 0
   dcp_reduce_epilogue<T, DCP_NRED, DCP_THREADS>(acc, p.red_out, p.partials, p.ticket);
 #endif
+#if DCP_GUARD
+  guard.flush(p.guard);
+#endif
 }
 #else
 // Batched form: many independent arrays (instances) run the same step
@@ -188,10 +196,12 @@ struct DcpBatchParams {
   int total_tiles;
   int seg;   // unused by the tile form
   int pad_;
+  unsigned long long* guard;  // first launch of a deferred run: largest |input| seen
 };
 
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
   extern __shared__ __align__(16) unsigned char dcp_smem[];
+  DcpGuard guard;
   for (int w = blockIdx.x; w < p.total_tiles; w += gridDim.x) {
     int lo = 0, hi = p.ninst - 1;
     while (lo < hi) {
@@ -205,7 +215,11 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
     T* A = reinterpret_cast<T*>(dcp_smem);
     T* B = A + DCP_TILE_ELEMS;
     const T* in = I.in;
-    dcp_tile(A, B, I.ny, I.nx, tyi, txi, [&](long long gi) { return in[gi]; });
+    dcp_tile(A, B, I.ny, I.nx, tyi, txi, [&](long long gi) {
+      const T v = in[gi];
+      if (DCP_GUARD) guard.see(v);
+      return v;
+    });
     for (int i = threadIdx.x; i < DCP_TX * DCP_TY; i += DCP_THREADS) {
       const int ty = i / DCP_TX, tx = i - ty * DCP_TX;
       const int gy = tyi * DCP_TY + ty, gx = txi * DCP_TX + tx;
@@ -214,5 +228,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
     }
     __syncthreads();  // the next work item overwrites the shared tile
   }
+#if DCP_GUARD
+  guard.flush(p.guard);
+#endif
 }
 #endif

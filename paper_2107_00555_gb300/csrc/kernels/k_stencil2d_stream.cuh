@@ -17,7 +17,7 @@
 // the largest arrays first in batched launches).
 //
 // The generated prefix defines DCP_T, DCP_C, DCP_RX, DCP_RY, DCP_NSTEPS,
-// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_PDM,
+// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_PDM, DCP_GUARD,
 // DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
 //   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
@@ -55,12 +55,21 @@ struct DcpItem {
   int y0, y1;    // rows written
 };
 
+// The lane's columns in a work item: the first one, and per column a bit
+// mask that keeps a value (all ones: the column lies inside the array) or
+// clears it to +0 (outside), computed once per item.
+struct DcpCols {
+  int col0;
+  typename DcpBits<T>::type keep[C];
+};
+
 // CHECK: the strip reaches outside the array (per-column tests).  ROWS: every
 // row touched by this iteration lies inside the array and outside a fixed
 // ring (no row tests).
 template <int L, int P, bool CHECK, bool ROWS>
 __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], int j,
-                                               const DcpItem& it, int col0, T (&outv)[C],
+                                               const DcpItem& it, const DcpCols& cols,
+                                               T (&outv)[C],
                                                bool& out_ok) {
   // level L (1-based) computes row y = j - L*RY from level L-1
   constexpr int l = L - 1;  // source level
@@ -103,10 +112,21 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
 #pragma unroll
       for (int c = 0; c < C; ++c) v[c] = dcp_epi<L - 1>(v[c]);
     }
+  } else if (DCP_BC == DCP_BC_ZERO) {
+    // columns outside the array read as ghost zeros at every level: the
+    // item's bit masks clear them (one bitwise AND per column, and exact for
+    // any value the epilogue leaves there, NaN included)
+    if (!row_in) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = (T)0;
+    } else {
+#pragma unroll
+      for (int c = 0; c < C; ++c) v[c] = dcp_keep(dcp_epi<L - 1>(v[c]), cols.keep[c]);
+    }
   } else {
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const int col = col0 + c;
+      const int col = cols.col0 + c;
       const bool in = row_in && (unsigned)col < (unsigned)it.nx;
       T r;
       if (!in) {
@@ -133,11 +153,12 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
 
 template <int L, int P, bool CHECK, bool ROWS>
 __device__ __forceinline__ void dcp_levels(T (&ring)[K > 1 ? K : 1][NR][C], int j,
-                                           const DcpItem& it, int col0, T (&outv)[C],
+                                           const DcpItem& it, const DcpCols& cols,
+                                           T (&outv)[C],
                                            bool& out_ok) {
   if constexpr (L <= K) {
-    dcp_level_step<L, P, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
-    dcp_levels<L + 1, P, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
+    dcp_level_step<L, P, CHECK, ROWS>(ring, j, it, cols, outv, out_ok);
+    dcp_levels<L + 1, P, CHECK, ROWS>(ring, j, it, cols, outv, out_ok);
   }
 }
 
@@ -148,13 +169,14 @@ __device__ __forceinline__ void dcp_levels(T (&ring)[K > 1 ? K : 1][NR][C], int 
 constexpr int PD = NR * (NR > 1 ? DCP_PDM : 2 * DCP_PDM);
 
 template <bool CHECK, bool ROWS, class Input>
-__device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem& it, int col0,
+__device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem& it,
+                                              const DcpCols& cols,
                                               Input& input) {
-  const long long base = (long long)j * it.nx + col0;
+  const long long base = (long long)j * it.nx + cols.col0;
   const bool row_ok = ROWS || (unsigned)j < (unsigned)it.ny;
 #pragma unroll
   for (int c = 0; c < C; ++c) {
-    const bool ok = row_ok && (!CHECK || (unsigned)(col0 + c) < (unsigned)it.nx);
+    const bool ok = row_ok && (!CHECK || (unsigned)(cols.col0 + c) < (unsigned)it.nx);
     dst[c] = ok ? input(base + c) : (T)0;
   }
 }
@@ -164,14 +186,17 @@ __device__ __forceinline__ void dcp_fetch_row(T (&dst)[C], int j, const DcpItem&
 // latency overlaps PD iterations of arithmetic.
 template <int P, bool CHECK, bool ROWS, class Input, class Output>
 __device__ __forceinline__ void dcp_iter(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
-                                         const DcpItem& it, int col0, Input& input,
-                                         Output& output) {
+                                         const DcpItem& it, const DcpCols& cols, Input& input,
+                                         Output& output, DcpGuard& guard) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) ring[0][P % NR][c] = q[P][c];
-  dcp_fetch_row<CHECK, ROWS>(q[P], j + PD, it, col0, input);
+  for (int c = 0; c < C; ++c) {
+    ring[0][P % NR][c] = q[P][c];
+    if (DCP_GUARD) guard.see(q[P][c]);  // arrived: requested PD iterations ago
+  }
+  dcp_fetch_row<CHECK, ROWS>(q[P], j + PD, it, cols, input);
   T outv[C];
   bool out_ok = false;
-  dcp_levels<1, P % NR, CHECK, ROWS>(ring, j, it, col0, outv, out_ok);
+  dcp_levels<1, P % NR, CHECK, ROWS>(ring, j, it, cols, outv, out_ok);
   const int y = j - K * DCP_RY;
   if (ROWS || (out_ok && y >= it.y0 && y < it.y1)) output(y, outv);
 }
@@ -179,39 +204,46 @@ __device__ __forceinline__ void dcp_iter(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)
 // Iterations j .. j + (PD - P) - 1 with phases P .. PD-1.
 template <int P, bool CHECK, bool ROWS, class Input, class Output>
 __device__ __forceinline__ void dcp_iters(T (&ring)[K > 1 ? K : 1][NR][C], T (&q)[PD][C], int j,
-                                          const DcpItem& it, int col0, Input& input,
-                                          Output& output) {
+                                          const DcpItem& it, const DcpCols& cols, Input& input,
+                                          Output& output, DcpGuard& guard) {
   if constexpr (P < PD) {
-    dcp_iter<P, CHECK, ROWS>(ring, q, j, it, col0, input, output);
-    dcp_iters<P + 1, CHECK, ROWS>(ring, q, j + 1, it, col0, input, output);
+    dcp_iter<P, CHECK, ROWS>(ring, q, j, it, cols, input, output, guard);
+    dcp_iters<P + 1, CHECK, ROWS>(ring, q, j + 1, it, cols, input, output, guard);
   }
 }
 
 // A single iteration of run-time phase r (alignment and tail), rows tested.
 template <int P, bool CHECK, class Input, class Output>
 __device__ __forceinline__ void dcp_iter_dyn(int r, T (&ring)[K > 1 ? K : 1][NR][C],
-                                             T (&q)[PD][C], int j, const DcpItem& it, int col0,
-                                             Input& input, Output& output) {
+                                             T (&q)[PD][C], int j, const DcpItem& it,
+                                             const DcpCols& cols,
+                                             Input& input, Output& output, DcpGuard& guard) {
   if constexpr (P < PD) {
-    if (r == P) dcp_iter<P, CHECK, false>(ring, q, j, it, col0, input, output);
-    else dcp_iter_dyn<P + 1, CHECK>(r, ring, q, j, it, col0, input, output);
+    if (r == P) dcp_iter<P, CHECK, false>(ring, q, j, it, cols, input, output, guard);
+    else dcp_iter_dyn<P + 1, CHECK>(r, ring, q, j, it, cols, input, output, guard);
   }
 }
 
 template <int P, bool CHECK, class Input>
-__device__ __forceinline__ void dcp_prefill(T (&q)[PD][C], int j0, const DcpItem& it, int col0,
+__device__ __forceinline__ void dcp_prefill(T (&q)[PD][C], int j0, const DcpItem& it,
+                                            const DcpCols& cols,
                                             Input& input) {
   if constexpr (P < PD) {
     // the row in [j0, j0 + PD) that maps to slot P
-    dcp_fetch_row<CHECK, false>(q[P], j0 + dcp_mod(P - j0, PD), it, col0, input);
-    dcp_prefill<P + 1, CHECK>(q, j0, it, col0, input);
+    dcp_fetch_row<CHECK, false>(q[P], j0 + dcp_mod(P - j0, PD), it, cols, input);
+    dcp_prefill<P + 1, CHECK>(q, j0, it, cols, input);
   }
 }
 
 template <bool CHECK, class Input, class Output>
-__device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input, Output& output) {
+__device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input, Output& output,
+                                                DcpGuard& guard) {
   const int lane = threadIdx.x & 31;
-  const int col0 = it.x0 - K * DCP_RX + lane * C;
+  DcpCols cols;
+  cols.col0 = it.x0 - K * DCP_RX + lane * C;
+#pragma unroll
+  for (int c = 0; c < C; ++c)
+    cols.keep[c] = (unsigned)(cols.col0 + c) < (unsigned)it.nx ? ~(typename DcpBits<T>::type)0 : 0;
   T ring[K > 1 ? K : 1][NR][C];
 #pragma unroll
   for (int l = 0; l < (K > 1 ? K : 1); ++l)
@@ -224,7 +256,7 @@ __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input,
   int j = it.y0 - K * DCP_RY;
   const int jend = it.y1 + K * DCP_RY;
   T q[PD][C];
-  dcp_prefill<0, CHECK>(q, j, it, col0, input);
+  dcp_prefill<0, CHECK>(q, j, it, cols, input);
   // Iterations [jb0, jb1) touch only rows inside the array (and outside a
   // fixed ring): level rows j - L*RY for L = 1..K, the fetched row j + PD and
   // the written row j - K*RY in [y0, y1).  They run without row tests.
@@ -236,10 +268,10 @@ __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input,
   const int jb1 = min(min(it.y1 + K * DCP_RY, it.ny - ring_w + DCP_RY), it.ny - PD);
   while (j < jend) {
     if (j >= jb0 && j + PD <= jb1 && dcp_mod(j, PD) == 0) {
-      dcp_iters<0, CHECK, true>(ring, q, j, it, col0, input, output);
+      dcp_iters<0, CHECK, true>(ring, q, j, it, cols, input, output, guard);
       j += PD;
     } else {
-      dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, col0, input, output);
+      dcp_iter_dyn<0, CHECK>(dcp_mod(j, PD), ring, q, j, it, cols, input, output, guard);
       ++j;
     }
   }
@@ -247,12 +279,14 @@ __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input,
 
 // Strips whose columns all lie inside the array (outside a fixed ring) take
 // the path without per-column boundary tests.
+// With DCP_GUARD every row the stream reads enters the magnitude guard.
 template <class Input, class Output>
-__device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Output&& output) {
+__device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, DcpGuard& guard,
+                                           Output&& output) {
   const int lo = DCP_BC == DCP_BC_FIXED_RING ? DCP_RX : 0;
   const int first = it.x0 - K * DCP_RX;
-  if (first >= lo && first + SPAN <= it.nx - lo) dcp_stream_impl<false>(it, input, output);
-  else dcp_stream_impl<true>(it, input, output);
+  if (first >= lo && first + SPAN <= it.nx - lo) dcp_stream_impl<false>(it, input, output, guard);
+  else dcp_stream_impl<true>(it, input, output, guard);
 }
 
 #if !DCP_BATCH
@@ -272,12 +306,14 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
+  DcpGuard guard;
   for (int w = warp; w < items; w += nwarps) {
     const int sg = w / strips, st = w - sg * strips;
     DcpItem it{nullptr, nullptr, ny, nx, st * W, sg * SEG, min(ny, (sg + 1) * SEG)};
     const int col0 = it.x0 - K * DCP_RX + lane * C;
     dcp_stream(
-        it, [&](long long gi) { return dcp_input(p, sc, gi); },
+        it,
+        [&](long long gi) { return dcp_input(p, sc, gi); }, guard,
         [&](int y, const T (&v)[C]) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
@@ -301,6 +337,9 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
 #if DCP_LAST && DCP_NRED > 0
   dcp_reduce_epilogue<T, DCP_NRED, DCP_THREADS>(acc, p.red_out, p.partials, p.ticket);
 #endif
+#if DCP_GUARD
+  guard.flush(p.guard);
+#endif
 }
 #else
 // Batched form: items are (instance, strip, row segment); instances are
@@ -317,12 +356,14 @@ struct DcpBatchParams {
   int total_tiles;
   int seg;   // rows per work item
   int pad_;
+  unsigned long long* guard;  // first launch of a deferred run: largest |input| seen
 };
 
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
+  DcpGuard guard;
   for (int w = warp; w < p.total_tiles; w += nwarps) {
     int lo = 0, hi = p.ninst - 1;
     while (lo < hi) {
@@ -338,7 +379,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
     T* out = I.out;
     const int col0 = it.x0 - K * DCP_RX + lane * C;
     dcp_stream(
-        it, [&](long long gi) { return in[gi]; },
+        it,
+        [&](long long gi) { return in[gi]; }, guard,
         [&](int y, const T (&v)[C]) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
@@ -348,5 +390,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
           }
         });
   }
+#if DCP_GUARD
+  guard.flush(p.guard);
+#endif
 }
 #endif

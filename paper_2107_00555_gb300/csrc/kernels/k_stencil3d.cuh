@@ -16,7 +16,7 @@
 // and the two weighted sums are independent chains of FP64 operations.
 //
 // The generated prefix defines DCP_T, DCP_TX, DCP_TY, DCP_TZ, DCP_RX,
-// DCP_RY, DCP_RZ, DCP_CX, DCP_AX, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST,
+// DCP_RY, DCP_RZ, DCP_CX, DCP_AX, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST, DCP_GUARD,
 // DCP_NLOAD, DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)
 //   void dcp_sum3(const T* const* pl, int c, T (&v)[DCP_CX])
@@ -67,9 +67,12 @@ __device__ __forceinline__ void dcp_fetch_plane(const DcpStParams& p, const T* s
     v[k] = (zok && off[k] >= 0) ? dcp_input(p, sc, zb + off[k]) : (T)0;
 }
 
-__device__ __forceinline__ void dcp_store_plane(T* dst, const T (&v)[DCP_LPT]) {
+// Stores a fetched plane into its ring slot (the loads have arrived by now:
+// with DCP_GUARD its values also enter the magnitude guard).
+__device__ __forceinline__ void dcp_store_plane(T* dst, const T (&v)[DCP_LPT], DcpGuard& guard) {
 #pragma unroll
   for (int k = 0; k < DCP_LPT; ++k) {
+    if (DCP_GUARD) guard.see(v[k]);
     const int i = threadIdx.x + k * DCP_THREADS;
     if (DCP_PLANE_LD % DCP_THREADS == 0 || i < DCP_PLANE_LD) {
       const int ly = i / DCP_LW, lx = i - ly * DCP_LW;
@@ -112,16 +115,17 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   }
 
   // ring slot of plane z: (z - z0 + RZ) mod NSLOT
+  DcpGuard guard;
   T pf[DCP_LPT];
   for (int dz = -DCP_RZ; dz < DCP_RZ; ++dz) {
     dcp_fetch_plane(p, sc, off, z0 + dz, pf);
-    dcp_store_plane(ring + ((dz + DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf);
+    dcp_store_plane(ring + ((dz + DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf, guard);
   }
   dcp_fetch_plane(p, sc, off, z0 + DCP_RZ, pf);
   for (int z = z0; z < z1; ++z) {
     // plane z + RZ goes into the slot last read while computing plane z - 2,
     // which every thread finished before the previous barrier
-    dcp_store_plane(ring + ((z - z0 + 2 * DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf);
+    dcp_store_plane(ring + ((z - z0 + 2 * DCP_RZ) % DCP_NSLOT) * DCP_PLANE, pf, guard);
     if (z + 1 < z1) dcp_fetch_plane(p, sc, off, z + DCP_RZ + 1, pf);
     __syncthreads();
     const T* pl[DCP_NP];
@@ -164,5 +168,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   }
 #if DCP_LAST && DCP_NRED > 0
   dcp_reduce_epilogue<T, DCP_NRED, DCP_THREADS>(acc, p.red_out, p.partials, p.ticket);
+#endif
+#if DCP_GUARD
+  guard.flush(p.guard);
 #endif
 }

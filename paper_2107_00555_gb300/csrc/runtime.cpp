@@ -44,6 +44,7 @@ struct StParamsH {
   int32_t seg, pad_;
   void* partials;
   void* ticket;
+  void* guard;
 };
 struct AxParamsH {
   const void* ld[kMaxIO];
@@ -68,8 +69,10 @@ struct BatchParamsH {
   int32_t total_tiles;
   int32_t seg;
   int32_t pad_;
+  void* guard;
 };
-static_assert(sizeof(StParamsH) == 5 * kMaxIO * 8 + 32 + 16, "stencil params layout");
+static_assert(sizeof(StParamsH) == 5 * kMaxIO * 8 + 32 + 24, "stencil params layout");
+static_assert(sizeof(BatchParamsH) == 32, "batch params layout");
 static_assert(sizeof(InstH) == 32, "instance layout");
 
 struct LaunchSpec {
@@ -101,6 +104,10 @@ struct GroupRT {
   int64_t ntickets = 0;
   std::vector<int64_t> offsets;  // batch: element offset of each member in a slab
   std::map<int, Table> tables;   // batch: per chunk
+  // magnitude guard of a deferred run: the largest finite |input| bit pattern
+  // its first launch saw, and the bound that keeps the run finite (0: none)
+  unsigned long long* guard = nullptr;
+  double guard_bound = 0.0;
 };
 
 int64_t numel(const std::vector<int64_t>& s) {
@@ -278,6 +285,10 @@ static void ensure_device(GraphImpl& g) {
       if (!G.reds.empty()) {
         R.ticket = (unsigned*)dalloc(rt, 256);
         check_cuda(cudaMemset(R.ticket, 0, 256), "cudaMemset(ticket)");
+      }
+      if (G.kind == GroupKind::Stencil || G.kind == GroupKind::Batch) {
+        R.guard = (unsigned long long*)dalloc(rt, 256);
+        check_cuda(cudaMemset(R.guard, 0, 256), "cudaMemset(guard)");
       }
     }
     check_cuda(cudaEventCreateWithFlags(&rt.table_ev, cudaEventDisableTiming), "cudaEventCreate");
@@ -487,6 +498,16 @@ static void launch_map(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
            "cuLaunchKernel(map)");
 }
 
+// Guard word of a launch that checks its input (first launch of a deferred
+// run): cleared on the launch stream (so a captured graph clears it too).
+static void* arm_guard(GraphImpl& g, const LaunchSpec& ls, cudaStream_t s) {
+  if (!(ls.code.guard_max_input > 0.0)) return nullptr;
+  GroupRT& R = g.rt->grt[ls.group];
+  R.guard_bound = ls.code.guard_max_input;
+  check_cuda(cudaMemsetAsync(R.guard, 0, sizeof(unsigned long long), s), "cudaMemsetAsync(guard)");
+  return R.guard;
+}
+
 static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
                            cudaStream_t s) {
   auto& rt = *g.rt;
@@ -538,6 +559,7 @@ static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const
     p.partials = group_partials(g, ls.group, gx * p.tiles_z);
     p.ticket = rt.grt[ls.group].ticket;
   }
+  p.guard = arm_guard(g, ls, s);
   void* args[] = {&p};
   check_cu(drv().launchKernel(ls.fn, (unsigned)gx, (unsigned)p.tiles_z, 1, ls.code.threads, 1, 1,
                               ls.code.smem_bytes, (CUstream)s, args, nullptr),
@@ -613,8 +635,9 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
     rt.table_ev_used = true;
     T.key = key;
   }
-  BatchParamsH p{T.dev, nm, T.tiles, G.seg, 0};
+  BatchParamsH p{T.dev, nm, T.tiles, G.seg, 0, nullptr};
   if (p.total_tiles == 0) return;
+  p.guard = arm_guard(g, ls, s);
   int64_t grid;
   if (G.variant == 1) {
     const int wpb = ls.code.threads / 32;
@@ -946,6 +969,40 @@ static void* mapped_address(const void* host) {
   return a.devicePointer;
 }
 
+// After the stream is idle: reports a deferred run whose input exceeded the
+// magnitude its scaled state keeps finite (the guard word is then cleared).
+static void check_guards(GraphImpl& g) {
+  if (!g.rt || !g.rt->device_ready) return;
+  auto& rt = *g.rt;
+  for (size_t gi = 0; gi < rt.grt.size(); ++gi) {
+    GroupRT& R = rt.grt[gi];
+    if (!R.guard || !(R.guard_bound > 0.0)) continue;
+    unsigned long long bits = 0;
+    check_cuda(cudaMemcpy(&bits, R.guard, sizeof bits, cudaMemcpyDeviceToHost), "cudaMemcpy(guard)");
+    const bool f32 = g.groups[gi].dtype == DCP_F32;
+    double seen;
+    if (f32) {
+      uint32_t b = (uint32_t)bits;
+      float f;
+      std::memcpy(&f, &b, 4);
+      seen = f;
+    } else {
+      std::memcpy(&seen, &bits, 8);
+    }
+    if (seen > R.guard_bound) {
+      check_cuda(cudaMemset(R.guard, 0, sizeof bits), "cudaMemset(guard)");
+      char msg[320];
+      std::snprintf(msg, sizeof msg,
+                    "a stencil input of magnitude %.3g exceeds %.3g, the largest the deferred "
+                    "common weight keeps finite for this stencil (its scaled state grows within a "
+                    "chunk of steps); results may have overflowed: set DCP_OPT_DEFERRED_WEIGHT = 0 "
+                    "before dcp_fuse for the plain weighted sum",
+                    seen, R.guard_bound);
+      fail(DCP_E_UNSUPPORTED, msg);
+    }
+  }
+}
+
 void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* outputs,
                     cudaStream_t s) {
   ensure_device(g);
@@ -971,6 +1028,7 @@ void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* output
     if (ok) {
       run_graph(g, din.data(), dout.data(), s);
       check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+      check_guards(g);
       return;
     }
   }
@@ -1000,12 +1058,13 @@ void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* output
                  "cudaMemcpyAsync(D2H)");
   }
   check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  check_guards(g);
 }
 
 void sync_graph(GraphImpl& g, cudaStream_t s) {
-  (void)g;
   check_cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
   check_cuda(cudaGetLastError(), "asynchronous CUDA error");
+  check_guards(g);
 }
 
 // ---------------------------------------------------------------------------

@@ -403,3 +403,35 @@ def test_plan_deferred_common_weight():
     g.output(v)
     g.fuse(C.DCP_FUSE_ALL)
     assert scales(g)[:4] == [1.0] * 4 and scales(g)[4] == pytest.approx(1e-5, rel=1e-15)
+
+
+def test_deferred_weight_option_and_run_start():
+    """DCP_OPT_DEFERRED_WEIGHT = 0 (before dcp_fuse) keeps the plain weighted
+    sum everywhere; the option takes 0 or 1 only and is frozen by dcp_fuse.
+    A deferred run begins at its group's first step (whose input the first
+    launch checks against the run's magnitude bound): equal steps after a
+    step of other weights keep the plain sum."""
+    def scales(g):
+        out = []
+        for l in g.plan()["launches"]:
+            out += l.get("deferred_scales", [None] * (l["steps"][1] - l["steps"][0]))
+        return out
+
+    g = programs.heat3d((8, 9, 10), 12, "periodic", "f64")
+    g.set_option(C.DCP_OPT_DEFERRED_WEIGHT, 0)
+    g.fuse(C.DCP_FUSE_ALL)
+    assert all(s is None for s in scales(g))
+    with pytest.raises(C.DcpError) as e:
+        g.set_option(C.DCP_OPT_DEFERRED_WEIGHT, 1)
+    assert e.value.status == C.DCP_E_STATE
+    g = programs.heat3d((8, 9, 10), 12, "periodic", "f64")
+    with pytest.raises(C.DcpError):
+        g.set_option(C.DCP_OPT_DEFERRED_WEIGHT, 2)
+    g = Graph()
+    v = g.input("f64", (8, 9, 10))
+    v = g.stencil(v, programs.SEVEN_POINT, [0.3] + [0.7 / 6] * 6, "periodic", 1)
+    for _ in range(4):
+        v = g.stencil(v, programs.SEVEN_POINT, programs.SEVEN_WEIGHTS, "periodic", 1)
+    g.output(v)
+    g.fuse(C.DCP_FUSE_ALL)
+    assert all(s is None for s in scales(g))

@@ -345,6 +345,80 @@ def test_jacobi2d_deferred_weight_forms_magnitudes_nan(bc):
     assert_close(got[ok], ref[ok], 1e-12, 1e290, "deferred weight 2-D %s" % bc)
 
 
+@pytest.mark.parametrize("prog", ["heat3d", "jacobi2d_tile", "jacobi2d_stream"])
+def test_deferred_weight_guard_reports_large_inputs(prog):
+    """An input above the magnitude the deferred common weight keeps finite
+    (about 1.8e299 for the heat step, 1.5e299 for the 5-point average) is
+    reported when the caller synchronises (DCP_E_UNSUPPORTED, naming the
+    option); with DCP_OPT_DEFERRED_WEIGHT = 0 the same program runs the plain
+    weighted sum and matches the oracle.  Inputs below the bound, and NaN /
+    inf inputs, are not reported."""
+    T = 12
+    if prog == "heat3d":
+        shape = (10, 12, 14)
+        build = lambda: programs.heat3d(shape, T, "periodic", "f64")
+        ref_prog = OP.heat3d(shape, T, "periodic")
+    else:
+        shape = (40, 70)
+        kernel = 0 if prog == "jacobi2d_tile" else 1
+
+        def build():
+            g = programs.jacobi2d(shape, T, "zero", "f64")
+            g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+            return g
+        ref_prog = OP.jacobi2d(shape, T, "zero")
+    u0 = inputs.uniform(shape, -1.0, 1.0, 27)
+    u0.flat[u0.size // 3] = 1e300
+    g = build()
+    g.fuse(FUSED)
+    g.run([to_dev(u0)])
+    with pytest.raises(C.DcpError) as e:
+        g.sync()
+    assert e.value.status == C.DCP_E_UNSUPPORTED and "DCP_OPT_DEFERRED_WEIGHT" in str(e.value)
+    g.sync()  # reported once
+    g0 = build()
+    g0.set_option(C.DCP_OPT_DEFERRED_WEIGHT, 0)
+    g0.fuse(FUSED)
+    assert all("deferred_scales" not in l for l in g0.plan()["launches"])
+    got = to_host(g0.run([to_dev(u0)])[0])
+    g0.sync()
+    ref = oracle.run(ref_prog, [u0])[-1]
+    assert_close(got, ref, 1e-12, 1e300, "plain sum on 1e300 inputs, %s" % prog)
+    # below the bound, and with NaN / inf: nothing to report
+    u1 = inputs.uniform(shape, -1.0, 1.0, 28) * 1e298
+    u1.flat[7] = np.nan
+    u1.flat[11] = np.inf
+    g.run([to_dev(u1)])
+    g.sync()
+
+
+def test_deferred_weight_guard_f32_batch_and_host_runs():
+    """float32 runs bound the growth by 2^16 (largest input about 2.2e34 for
+    the 5-point average): a batch with one instance above it is reported; the
+    host-buffer entry point, which waits for its stream, reports it directly;
+    the option turns the deferral off and the batch matches the oracle."""
+    sides = [40, 70, 33]
+    T = 20
+    host = [inputs.uniform((s, s), 0.0, 1.0, 30 + i).astype(np.float32) for i, s in enumerate(sides)]
+    host[1][3, 4] = np.float32(1e35)
+    g = programs.batch2d(sides, T, "zero", "f32", fuse=FUSED | C.DCP_BATCH)
+    g.run([to_dev(a) for a in host])
+    with pytest.raises(C.DcpError) as e:
+        g.sync()
+    assert e.value.status == C.DCP_E_UNSUPPORTED
+    with pytest.raises(C.DcpError) as e:
+        g.run_host(host)
+    assert e.value.status == C.DCP_E_UNSUPPORTED
+    g0 = programs.batch2d(sides, T, "zero", "f32")
+    g0.set_option(C.DCP_OPT_DEFERRED_WEIGHT, 0)
+    g0.fuse(FUSED | C.DCP_BATCH)
+    outs = g0.run([to_dev(a) for a in host])
+    g0.sync()
+    for a, o in zip(host, outs):
+        ref = oracle.run(OP.jacobi2d(a.shape, T, "zero"), [a])[-1]
+        assert_close(to_host(o), ref, 1e-5, float(np.max(np.abs(a))), "f32 batch, plain sum")
+
+
 def test_radius2_3d_stencil_paired_cells():
     shape = (12, 14, 37)
     offs = [(0, 0, 0), (0, 0, -2), (0, 0, 2), (0, -2, 0), (0, 2, 0), (-2, 0, 0), (2, 0, 0),

@@ -11,6 +11,8 @@ backward-stable bound, exact max / min, wrapped integer sums), and a
 warmed-up call must leave the device's free memory unchanged.
 This file is collected last on purpose.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -98,6 +100,7 @@ def test_noalloc_matches_oracle_and_allocates_nothing(dtype, red):
     # warm-up: the first call on a device looks up the scratch and loads the kernel
     C.dcp_reduce_noalloc(xd.data_ptr(), n, CODES[dtype], REDS[red], out.data_ptr(), s)
     torch.cuda.synchronize()
+    gc.collect()  # tensors of earlier tests freed now, not inside the measured calls
     free0, _ = torch.cuda.mem_get_info()
     torch_bytes0 = torch.cuda.memory_allocated()
     for _ in range(2):
@@ -114,4 +117,4 @@ def test_noalloc_matches_oracle_and_allocates_nothing(dtype, red):
             assert float(got) == want, (got, want)
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0, (free0, free1)
-    assert torch.cuda.memory_allocated() == torch_bytes0
+    assert torch.cuda.memory_allocated() <= torch_bytes0  # nothing through torch's allocator

@@ -1219,7 +1219,8 @@ def run_reference(args):
 
 def run_probe(args):
     """The FP64 rate of this GPU for each binary64 operation (the roofline
-    denominator of the f64 workloads), with the SM clocks sampled meanwhile."""
+    denominator of the f64 workloads; an add is also timed as a fused
+    multiply-add by a run-time 1.0), with the SM clocks sampled meanwhile."""
     import torch
     from paper_2107_00555_gb300 import _capi as C
     torch.cuda.set_device(0)
@@ -1227,7 +1228,7 @@ def run_probe(args):
     C.dcp_probe_fp64(0, 8192, stream.cuda_stream)  # load the module, wake the clocks
     res = {}
     with ClockSampler(0) as clk:
-        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+        for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul"), (3, "dadd_as_dfma")):
             runs = [C.dcp_probe_fp64(op, 65536, stream.cuda_stream) for _ in range(5)]
             res[name] = {"ginst_s": round(max(g for g, _ in runs), 2),
                          "median_ginst_s": round(statistics.median(g for g, _ in runs), 2),

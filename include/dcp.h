@@ -154,15 +154,17 @@ dcp_status dcp_add_map(dcp_graph g, int32_t op, int32_t n_in, const dcp_value* i
  * axis contiguous), boundary rule `bc`.  Floating dtypes, 1..3 axes,
  * 1 <= npoints <= 32, |offset| <= 4 per axis, steps >= 0.  Rounding: each
  * step is one multiply and FMAs in point order, except on a deferred common
- * weight: a run of two or more steps with a zero or periodic boundary,
- * beginning at the first step of its fused group, whose weights are exact
- * multiples of one weight f, sums the exact ratios w_k / f and applies f^m
- * every m steps, m bounded so that the scaled state grows by at most 2^32
- * (float64) or 2^16 (float32).  Such a run keeps finite results for inputs
- * up to the type's largest value over that growth (about 1.8e299 for the
- * heat step, 2.2e34 for a float32 five-point average); its first launch
- * records the largest finite |input| it reads, and dcp_sync (or
- * dcp_run_host) returns DCP_E_UNSUPPORTED when that exceeds the run's bound.
+ * weight: a run of two or more steps with a zero or periodic boundary whose
+ * weights are exact multiples of one weight f sums the exact ratios w_k / f
+ * and applies f^m every m steps, m bounded so that the scaled state grows by
+ * at most 2^32 (float64 only).  Such a run keeps finite results for inputs
+ * up to the largest double over that growth (about 1.8e299 for the heat
+ * step, 1.5e299 for the five-point average).  When the run
+ * begins at the first step of its fused group (a stencil node's own steps,
+ * or a chain of equal nodes), its first launch records the largest finite
+ * |input| it reads, and dcp_sync (or dcp_run_host) returns
+ * DCP_E_UNSUPPORTED when that exceeds the run's bound; a run that begins
+ * after an epilogue map inside a group is not checked.
  * DCP_OPT_DEFERRED_WEIGHT = 0 selects the plain weighted sum throughout. */
 dcp_status dcp_add_stencil(dcp_graph g, dcp_value in, int32_t npoints, const int32_t* offsets,
                            const double* weights, int32_t bc, int32_t steps, dcp_value* out);
@@ -275,7 +277,8 @@ dcp_status dcp_reduce_noalloc(const void* in, int64_t n, int32_t dtype, int32_t 
  * operations per thread and chain count; 4, 8 and 16 chains per thread are
  * each timed with CUDA events on `cuda_stream` after a shorter warm-up
  * launch, and the best rate is returned.
- *   op     0 = fused multiply-add, 1 = add, 2 = multiply (binary64)
+ *   op     0 = fused multiply-add, 1 = add, 2 = multiply, 3 = add issued as
+ *          a fused multiply-add by a run-time 1.0 (binary64)
  *   iters  1 .. 2^24 operations per chain (8192 runs for tens of ms on GB300)
  *   gops   receives 10^9 lane operations per second (a fused multiply-add
  *          counts once here; it is 2 flops)

@@ -299,11 +299,10 @@ void emit_stencil_io(std::ostringstream& os, const GraphImpl& g, const Group& G,
 // depends only on its place in its run, so every kernel form, tile shape,
 // time-tile depth and split into launches computes the same bits.
 //
-// binary32 steps (the batched and other float32 stencils, bound by
-// instruction issue) take the same form on their float32-rounded weights,
-// with chunks of (sum |r_k|)^D <= 2^16 (float32 spans only 2^128: inputs up
-// to about 2^112, 5e33, stay finite) and f^m rounded once to float32 from
-// its binary64 value.
+// binary32 steps keep the plain sum: the float32 stencils are bound by
+// instruction issue and memory latency, not by their arithmetic, and the
+// deferred form measured no faster on the batched workload (slower at some
+// time-tile depths).
 struct Defer {
   bool on = false;
   std::vector<int> order;     // point order: a ratio-1 point first
@@ -342,15 +341,12 @@ bool defer_ratios(const std::vector<double>& w, std::vector<double>& ratio, doub
 // stencil node n's steps; 0 when its steps keep the plain weighted sum.
 // Unbounded growth limits (sum |r_k| <= 1) give INT32_MAX.
 int defer_chunk_steps(const Node& n) {
-  const bool f32 = n.dtype == DCP_F32;
-  if ((n.dtype != DCP_F64 && !f32) || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return 0;
-  std::vector<double> r, w = n.weights;
-  if (f32)
-    for (double& x : w) x = (double)(float)x;
+  if (n.dtype != DCP_F64 || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return 0;
+  std::vector<double> r;
   double f = 0.0, gsum = 0.0;
-  if (!defer_ratios(w, r, f, gsum)) return 0;
+  if (!defer_ratios(n.weights, r, f, gsum)) return 0;
   if (gsum <= 1.0) return INT32_MAX;
-  const int D = (int)std::floor((f32 ? 16.0 : 32.0) / std::log2(gsum));
+  const int D = (int)std::floor(32.0 / std::log2(gsum));
   return D >= 2 ? D : 0;
 }
 
@@ -359,8 +355,7 @@ namespace {
 Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   Defer d;
   const Node& n = g.nodes[G.steps[s].node];
-  const bool f32 = n.dtype == DCP_F32;
-  if ((n.dtype != DCP_F64 && !f32) || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return d;
+  if (n.dtype != DCP_F64 || (n.bc != DCP_BC_ZERO && n.bc != DCP_BC_PERIODIC)) return d;
   auto opt = g.options.find(DCP_OPT_DEFERRED_WEIGHT);
   if (opt != g.options.end() && opt->second == 0) return d;
   const int S = (int)G.steps.size();
@@ -375,25 +370,17 @@ Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   int b = s + 1;
   while (b < S && same(b) && G.steps[b - 1].epi.empty()) ++b;
   const int L = b - a;
-  // a run begins at the group's first step, whose input the first launch
-  // reads and checks (the magnitude guard); later runs keep the plain sum
-  if (L < 2 || a != 0) return d;
-  std::vector<double> r, w = n.weights;
-  if (f32)
-    for (double& x : w) x = (double)(float)x;  // the kernel's float32 weights
+  if (L < 2) return d;
+  std::vector<double> r;
   double f = 0.0, gsum = 0.0;
-  if (!defer_ratios(w, r, f, gsum)) return d;
+  if (!defer_ratios(n.weights, r, f, gsum)) return d;
   const int Dmax = defer_chunk_steps(n);
   if (Dmax == 0) return d;
   const int D = std::min(L, Dmax);
   if (D < 2) return d;
-  auto power = [f, f32](int m) {
+  auto power = [f](int m) {
     double F = 1.0;
     for (int t = 0; t < m; ++t) F *= f;
-    if (f32) {
-      const float F32 = (float)F;
-      return std::isnormal(F32) ? (double)F32 : 0.0;
-    }
     return std::isnormal(F) ? F : 0.0;
   };
   if (power(D) == 0.0 || (L % D != 0 && power(L % D) == 0.0)) return d;
@@ -412,7 +399,7 @@ Defer plan_defer(const GraphImpl& g, const Group& G, int s) {
   // the scaled state of a chunk of D steps is at most (sum |r_k|)^D times the
   // largest |input| (sum |r_k| <= 1: no growth)
   const double growth = gsum <= 1.0 ? 1.0 : std::pow(gsum, (double)D);
-  d.max_input = (f32 ? (double)FLT_MAX : DBL_MAX) / growth;
+  d.max_input = DBL_MAX / growth;
   return d;
 }
 

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(kThreads) fp64_probe_kernel(long long iters, d
     for (int k = 0; k < CHAINS; ++k) {
       if (OP == 0) a[k] = __fma_rn(a[k], bb[k], cc[k]);
       else if (OP == 1) a[k] = __dadd_rn(a[k], cc[k]);
-      else a[k] = __dmul_rn(a[k], bb[k]);
+      else if (OP == 2) a[k] = __dmul_rn(a[k], bb[k]);
+      else a[k] = __fma_rn(a[k], b, cc[k]);  // an add issued as a fused multiply-add by b = 1
     }
   }
 #pragma unroll
@@ -53,8 +54,10 @@ __global__ void __launch_bounds__(kThreads) fp64_probe_kernel(long long iters, d
 // binary64 operations it performed.
 template <int OP, int CHAINS>
 float launch_and_time(long long iters, cudaStream_t s, double* lane_ops) {
-  // b slightly below 1 and c small keep every chain finite and normal
-  const double b = 0.9999999, c = 1e-7, sentinel = -12345.678;
+  // b slightly below 1 (exactly 1 for the add issued as a fused
+  // multiply-add, a value the compiler cannot see) and c small keep every
+  // chain finite and normal
+  const double b = OP == 3 ? 1.0 : 0.9999999, c = 1e-7, sentinel = -12345.678;
   int dev = 0, sms = 0, per_sm = 0;
   dcp::check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
   dcp::check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
@@ -98,12 +101,15 @@ extern "C" dcp_status dcp_probe_fp64(int32_t op, int64_t iters, double* gops, do
                                      void* cuda_stream) {
   try {
     if (!gops) dcp::fail(DCP_E_INVALID_ARG, "gops is NULL");
-    if (op < 0 || op > 2) dcp::fail(DCP_E_INVALID_ARG, "op must be 0 (fma), 1 (add) or 2 (mul)");
+    if (op < 0 || op > 3)
+      dcp::fail(DCP_E_INVALID_ARG, "op must be 0 (fma), 1 (add), 2 (mul) or 3 (add as fma by 1)");
     if (iters < 1 || iters > (1ll << 24)) dcp::fail(DCP_E_INVALID_ARG, "iters must be in [1, 2^24]");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     float t = 0.f;
-    double g = op == 0 ? best_rate<0>(iters, s, &t)
-                       : (op == 1 ? best_rate<1>(iters, s, &t) : best_rate<2>(iters, s, &t));
+    double g = op == 0   ? best_rate<0>(iters, s, &t)
+               : op == 1 ? best_rate<1>(iters, s, &t)
+               : op == 2 ? best_rate<2>(iters, s, &t)
+                         : best_rate<3>(iters, s, &t);
     if (!(g > 0.0)) dcp::fail(DCP_E_CUDA, "FP64 probe timed at zero");
     *gops = g;
     if (ms) *ms = t;

@@ -700,8 +700,9 @@ static void launch_all(GraphImpl& g, const std::vector<const void*>& ptr, cudaSt
 // ---------------------------------------------------------------------------
 namespace {
 // A tuned configuration: depth, tz, ty, tx, and for 3-D stencils the cells
-// per thread along x (stream kernels: tz = -1, ty = rows per item, tx =
-// prefetch depth).
+// per thread along x, for 2-D tile kernels the threads per CTA (32 or more;
+// smaller values mean the default 256) (stream kernels: tz = -1, ty = rows
+// per item, tx = prefetch depth).
 typedef std::array<int, 5> TuneCfg;
 std::mutex g_tune_mu;
 std::map<std::string, TuneCfg> g_tune_cache;  // signature -> configuration
@@ -776,6 +777,7 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
   // small binary64 grids are bound by the FP64 pipes of the SMs they occupy:
   // tile shapes whose count is at most one or two per SM balance that work
   // (e.g. 152 tiles of 14 x 32 on a 256 x 256 grid)
+  size_t balanced = 0;
   if (nd == 2 && G.kind != GroupKind::Batch && G.dtype == DCP_F64 && sms > 0) {
     const int64_t ny = G.shape[0], nx = G.shape[1];
     for (int per_sm : {1, 2})
@@ -784,15 +786,25 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
         const int64_t rows = (int64_t)per_sm * sms / tiles_x;
         if (rows < 1) continue;
         const int64_t ty = (ny + rows - 1) / rows;
-        if (ty >= 4 && ty <= 256 && tiles_x * ((ny + ty - 1) / ty) * 2 > (int64_t)per_sm * sms)
+        if (ty >= 4 && ty <= 256 && tiles_x * ((ny + ty - 1) / ty) * 2 > (int64_t)per_sm * sms) {
           tiles.push_back({(int)ty, tx});
+          ++balanced;
+        }
       }
   }
+  const size_t base_tiles = tiles.size() - balanced;
   for (int d : depths)
-    for (const auto& t : tiles) {
+    for (size_t i = 0; i < tiles.size(); ++i) {
+      const auto& t = tiles[i];
       int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
       long smem = 2L * (t[0] + 2 * d * ry) * (t[1] + 2 * d * rx) * dtype_size(G.dtype);
-      if (smem <= 160 * 1024) c.push_back({d, 1, t[0], t[1], 1});
+      if (smem > 160 * 1024) continue;
+      c.push_back({d, 1, t[0], t[1], 1});
+      // the balanced tiles also with 512 and 1024 threads: one cell per
+      // thread keeps hundreds of independent FP64 chains in flight per SM,
+      // which a latency-bound small grid needs
+      if (i >= base_tiles)
+        for (int th : {512, 1024}) c.push_back({d, 1, t[0], t[1], th});
     }
   // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item,
   // 0 = planner's; tx slot = row windows requested ahead)
@@ -836,7 +848,7 @@ void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
       G.seg = (int)std::min<int64_t>(std::max<int64_t>(seg, 1), std::max<int64_t>(ny, 1));
     }
   } else {
-    G.threads = 256;
+    G.threads = group_nd(G) == 3 || cfg[4] < 32 ? 256 : cfg[4];
   }
   std::vector<LaunchSpec> L = build_group_launches(g, gi);
   for (auto& ls : L) load_launch(ls);

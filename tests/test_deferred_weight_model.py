@@ -1,17 +1,16 @@
-"""The deferred common weight of the stencil kernels, replayed on the host.
+"""The deferred common weight of the binary64 stencil kernels, replayed on the
+host.
 
 A step whose weights are all exact multiples w_k = f r_k of one weight f sums
 the ratios on the state scaled by 1/f^t (the first point of ratio 1 with no
 multiply, then the other points in the listed order: an add for ratio 1, an
 exact r x plus one rounding for the power-of-two ratios used here), and f^m
 is applied after every chunk of m <= D steps.  D comes from the planner
-itself (dcp_plan_info's per-step factors): (sum |r_k|)^D <= 2^32 for
-binary64, 2^16 for binary32.  Against the oracle's plain weighted sum this
-keeps long runs within the dtype's tolerance, and the scaled state stays
-finite for inputs up to the bound the chunk length gives.  Each operation of
-the model is one IEEE rounding in the step's dtype (numpy float32 / float64
-adds; f^m is the product of m binary64 roundings, rounded once to float32
-for binary32)."""
+itself (dcp_plan_info's per-step factors): (sum |r_k|)^D <= 2^32.  Against
+the oracle's plain weighted sum this keeps long runs within the f64
+tolerance, and the scaled state stays finite for inputs up to the bound the
+chunk length gives.  Each operation of the model is one IEEE rounding
+(numpy float64 adds; f^m is the product of m roundings of f)."""
 import math
 
 import numpy as np
@@ -35,9 +34,9 @@ SETS = [
 ]
 
 
-def _planner_scales(shape, offs, w, bc, T, dtype):
+def _planner_scales(shape, offs, w, bc, T):
     g = Graph()
-    x = g.input(dtype, shape)
+    x = g.input("f64", shape)
     g.output(g.stencil(x, offs, w, bc, T))
     g.fuse(C.DCP_FUSE_ALL)
     out = []
@@ -59,15 +58,13 @@ def _shift(a, off, bc):
     return out
 
 
-def _deferred_run(u0, offs, w, bc, T, dtype, D):
-    np_t = np.float32 if dtype == "f32" else np.float64
-    wt = [float(np_t(x)) for x in w]
-    f = max(set(wt), key=wt.count)
-    r = [x / f for x in wt]
-    assert all(x * f == y for x, y in zip(r, wt))
+def _deferred_run(u0, offs, w, bc, T, D):
+    f = max(set(w), key=w.count)
+    r = [x / f for x in w]
+    assert all(x * f == y for x, y in zip(r, w))
     first = r.index(1.0)
     order = [first] + [k for k in range(len(r)) if k != first]
-    s = u0.astype(np_t)
+    s = u0.astype(np.float64)
     for t in range(T):
         nb = [_shift(s, offs[k], bc) for k in range(len(offs))]
         acc = nb[order[0]].copy()
@@ -76,14 +73,14 @@ def _deferred_run(u0, offs, w, bc, T, dtype, D):
                 acc = acc + nb[k]
             else:  # power-of-two ratio: r x exact, one rounding
                 assert math.frexp(abs(r[k]))[0] == 0.5
-                acc = np_t(r[k]) * nb[k] + acc
+                acc = r[k] * nb[k] + acc
         i = t + 1
         m = D if i % D == 0 else (T % D if i == T else 0)
         if m:
             F = 1.0
             for _ in range(m):
                 F *= f
-            acc = np_t(F) * acc
+            acc = F * acc
         s = acc
     return s
 
@@ -96,49 +93,39 @@ def _chunk(scales):
     return None
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("name,offs,w", SETS)
 @pytest.mark.parametrize("bc", ["periodic", "zero"])
-def test_long_runs_within_tolerance(dtype, name, offs, w, bc):
+def test_long_runs_within_tolerance(name, offs, w, bc):
     if name == "heat":
         shape = (9, 10, 11)
         Ts = (9, 50, 121)
     else:
         shape = (23, 29)
         Ts = (13, 60, 301)
-    gsum = sum(abs(x / w[-1]) if name != "heat" else abs(x / 0.1) for x in w)
-    bits = 16 if dtype == "f32" else 32
-    D = int(math.floor(bits / math.log2(gsum)))
+    f = max(set(w), key=w.count)
+    D = int(math.floor(32 / math.log2(sum(abs(x / f) for x in w))))
     u0 = inputs.uniform(shape, -1.0, 1.0, 31)
-    if dtype == "f32":
-        u0 = u0.astype(np.float32)
     for T in Ts:
-        sc = _planner_scales(shape, offs, w, bc, T, dtype)
-        assert len(sc) == T and all(x is not None for x in sc), (name, dtype, T)
+        sc = _planner_scales(shape, offs, w, bc, T)
+        assert len(sc) == T and all(x is not None for x in sc), (name, T)
         if T > D:
-            assert _chunk(sc) == D, (name, dtype, T, sc[:D + 1])
-        ref = oracle.stencil(u0.astype(np.float64), offs,
-                             [float(np.float32(x)) for x in w] if dtype == "f32" else w, bc, T)
-        got = _deferred_run(u0, offs, w, bc, T, dtype, D).astype(np.float64)
+            assert _chunk(sc) == D, (name, T, sc[:D + 1])
+        ref = oracle.stencil(u0, offs, w, bc, T)
+        got = _deferred_run(u0, offs, w, bc, T, D)
         scale = float(np.max(np.abs(u0)))
         # the negative-weight step amplifies the state: compare relative to the
         # largest reference value
         if name == "negative":
             scale = max(scale, float(np.max(np.abs(ref))))
-        tol = 1e-5 if dtype == "f32" else 1e-12
-        assert np.all(np.abs(got - ref) <= tol * np.maximum(np.abs(ref), scale)), (name, dtype, T)
+        assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(np.abs(ref), scale)), (name, T)
 
 
-@pytest.mark.parametrize("dtype,big", [("f64", 1e298), ("f32", 5e33)])
-def test_scaled_state_stays_finite_up_to_the_bound(dtype, big):
+def test_scaled_state_stays_finite_up_to_the_bound():
     name, offs, w = SETS[0]
-    np_t = np.float32 if dtype == "f32" else np.float64
-    u0 = inputs.uniform((6, 7, 8), -1.0, 1.0, 32).astype(np_t)
-    u0[0, 0, 0] = big
-    D = _chunk(_planner_scales(u0.shape, offs, w, "periodic", 18, dtype))
-    got = _deferred_run(u0, offs, w, "periodic", 18, dtype, D)
+    u0 = inputs.uniform((6, 7, 8), -1.0, 1.0, 32)
+    u0[0, 0, 0] = 1e298
+    D = _chunk(_planner_scales(u0.shape, offs, w, "periodic", 18))
+    got = _deferred_run(u0, offs, w, "periodic", 18, D)
     assert np.isfinite(got).all()
-    wts = [float(np.float32(x)) for x in w] if dtype == "f32" else w
-    ref = oracle.stencil(u0.astype(np.float64), offs, wts, "periodic", 18)
-    tol = 1e-5 if dtype == "f32" else 1e-12
-    assert np.max(np.abs(got.astype(np.float64) - ref)) <= tol * big
+    ref = oracle.stencil(u0, offs, w, "periodic", 18)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * 1e298

@@ -246,6 +246,25 @@ def test_autotune_picks_a_config_and_keeps_results():
     assert plan["n_launches"] == -(-12 // grp["depth"])
 
 
+def test_autotune_small_f64_grid_keeps_bits():
+    """The 256^2 binary64 five-point program (10 steps): the autotuner also
+    tries tile shapes balanced over the SMs with 256, 512 and 1024 threads;
+    whatever it keeps computes the same bits as the untuned plan, within the
+    f64 tolerance of the oracle."""
+    u0 = inputs.cfg1(seed=43, n=256)
+    ref = oracle.run(OP.jacobi2d((256, 256), 10, "zero"), [u0])[-1]
+    g0 = programs.jacobi2d((256, 256), 10, "zero", "f64", fuse=C.DCP_FUSE_ALL)
+    want = to_host(g0.run([to_dev(u0)])[0]).copy()
+    g = programs.jacobi2d((256, 256), 10, "zero", "f64")
+    g.set_option(C.DCP_OPT_USE_GRAPH, 1)
+    g.fuse(C.DCP_FUSE_ALL | C.DCP_AUTOTUNE)
+    d = to_dev(u0)
+    o1 = to_host(g.run([d])[0]).copy()   # tuning run
+    o2 = to_host(g.run([d])[0]).copy()   # tuned run (graph replay)
+    assert o1.tobytes() == want.tobytes() == o2.tobytes()
+    assert_close(o2, ref, 1e-12, 1.0, "tuned 256^2 f64")
+
+
 @pytest.mark.parametrize("direct", [1, 0])
 def test_run_host_pinned_buffers(direct):
     """Page-locked host buffers: the kernels access them directly (or, with
@@ -393,10 +412,10 @@ def test_fp64_probe_reports_a_plausible_rate():
     torch.cuda.init()
     s = torch.cuda.current_stream().cuda_stream
     cap = 152 * 128 * 2.1
-    for op in (0, 1, 2):
+    for op in (0, 1, 2, 3):
         g, ms = C.dcp_probe_fp64(op, 1024, s)
         assert 0 < g < cap and ms > 0, (op, g, ms)
     with pytest.raises(C.DcpError):
-        C.dcp_probe_fp64(3, 1024, s)
+        C.dcp_probe_fp64(4, 1024, s)
     with pytest.raises(C.DcpError):
         C.dcp_probe_fp64(0, 0, s)

@@ -122,8 +122,10 @@ enum {
   DCP_OPT_STREAM_THREADS = 12, /* warp-stream stencils: threads per CTA (32..1024, multiple of 32; default 64) */
   DCP_OPT_CELLS_PER_THREAD = 13, /* 3-D stencils: cells per thread along x (1 or 2) */
   DCP_OPT_MAP_UNROLL = 14,      /* map kernels: 16-byte vectors per array in flight per thread (1..8) */
-  DCP_OPT_DEFERRED_WEIGHT = 15  /* stencils: 1 (default) deferred common weight where it applies,
+  DCP_OPT_DEFERRED_WEIGHT = 15, /* stencils: 1 (default) deferred common weight where it applies,
                                    0 the plain weighted sum everywhere (set before dcp_fuse) */
+  DCP_OPT_STREAM_MIN_CTAS = 16  /* warp-stream stencils: CTAs per SM the register budget must
+                                   allow (1..32; default: the compiler's choice) */
 };
 
 /* ---- graph construction ------------------------------------------------ */

@@ -53,6 +53,7 @@ DCP_OPT_STREAM_THREADS = 12
 DCP_OPT_CELLS_PER_THREAD = 13
 DCP_OPT_MAP_UNROLL = 14
 DCP_OPT_DEFERRED_WEIGHT = 15
+DCP_OPT_STREAM_MIN_CTAS = 16
 
 _STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("DCP_E_") or k == "DCP_OK"}
 

@@ -383,6 +383,7 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
       case DCP_OPT_CELLS_PER_THREAD:
       case DCP_OPT_MAP_UNROLL:
       case DCP_OPT_DEFERRED_WEIGHT:
+      case DCP_OPT_STREAM_MIN_CTAS:
         if (g.fused) fail(DCP_E_STATE, "tiling options must be set before dcp_fuse");
         break;
       case DCP_OPT_USE_GRAPH:
@@ -406,6 +407,7 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
     if (key == DCP_OPT_CELLS_PER_THREAD && v != 1 && v != 2) fail(DCP_E_INVALID_ARG, "cells per thread must be 1 or 2");
     if (key == DCP_OPT_MAP_UNROLL && (v < 1 || v > 8)) fail(DCP_E_INVALID_ARG, "map unroll must be in 1..8");
     if (key == DCP_OPT_DEFERRED_WEIGHT && v != 0 && v != 1) fail(DCP_E_INVALID_ARG, "deferred weight must be 0 or 1");
+    if (key == DCP_OPT_STREAM_MIN_CTAS && (v < 1 || v > 32)) fail(DCP_E_INVALID_ARG, "stream min CTAs must be in 1..32");
     g.options[key] = v;
   });
 }

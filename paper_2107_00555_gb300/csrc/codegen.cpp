@@ -457,6 +457,7 @@ static CodegenOut gen_stream_kernel(const GraphImpl& g, const Group& G, int s0, 
      << "\n#define DCP_PDM " << G.prefetch << "\n";
   const Defer guard = first ? plan_defer(g, G, 0) : Defer();
   os << "#define DCP_GUARD " << (guard.on ? 1 : 0) << "\n";
+  if (G.min_ctas > 0) os << "#define DCP_MINB " << G.min_ctas << "\n";
   os << red_op_fn(g, last ? G.reds : std::vector<int>{});
   os << "#include \"dcp_device.cuh\"\n";
   if (!batch) emit_stencil_io(os, g, G, first, last);

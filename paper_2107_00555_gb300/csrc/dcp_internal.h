@@ -131,6 +131,7 @@ struct Group {
   int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
   int seg = 0;                  // warp stream: rows per work item (single arrays)
   int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
+  int min_ctas = 0;             // warp stream: CTAs per SM the register budget must allow (0: any)
   int cx = 1;                   // 3-D stencils: cells per thread along x (1 or 2)
   int unroll = 2;               // map groups: 16-byte vectors per array in flight per thread
   // axis-reduce groups: the reduced axis of the iteration space `shape`

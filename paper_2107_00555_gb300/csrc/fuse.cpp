@@ -486,6 +486,7 @@ struct Planner {
     if (var == 1) {
       G.threads = (int)opt(DCP_OPT_STREAM_THREADS, 64);
       G.prefetch = (int)opt(DCP_OPT_STREAM_PREFETCH, 1);
+      G.min_ctas = (int)opt(DCP_OPT_STREAM_MIN_CTAS, 0);
       if (G.kind == GroupKind::Batch) {
         G.seg = 64;  // rows per work item: short, uniform items balance the batch
       } else {

@@ -17,7 +17,7 @@
 // the largest arrays first in batched launches).
 //
 // The generated prefix defines DCP_T, DCP_C, DCP_RX, DCP_RY, DCP_NSTEPS,
-// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_PDM, DCP_GUARD,
+// DCP_BC, DCP_THREADS, DCP_KNAME, DCP_BATCH, DCP_LAST, DCP_PDM, DCP_GUARD, DCP_MINB,
 // DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
 //   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
@@ -29,6 +29,9 @@
 typedef DCP_T T;
 typedef typename DcpFin<T>::type F;
 #define DCP_ARR(n) ((n) > 0 ? (n) : 1)
+#ifndef DCP_MINB
+#define DCP_MINB 1   // CTAs per SM the compiler's register budget must allow
+#endif
 
 #define DCP_BC_ZERO 0
 #define DCP_BC_PERIODIC 1
@@ -285,13 +288,15 @@ __device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, Dcp
                                            Output&& output) {
   const int lo = DCP_BC == DCP_BC_FIXED_RING ? DCP_RX : 0;
   const int first = it.x0 - K * DCP_RX;
-  if (first >= lo && first + SPAN <= it.nx - lo) dcp_stream_impl<false>(it, input, output, guard);
-  else dcp_stream_impl<true>(it, input, output, guard);
+  if (first >= lo && first + SPAN <= it.nx - lo)
+    dcp_stream_impl<false>(it, input, output, guard);
+  else
+    dcp_stream_impl<true>(it, input, output, guard);
 }
 
 #if !DCP_BATCH
 // Single array: items = strips x row segments of p.seg rows.
-extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStParams p) {
+extern "C" __global__ void __launch_bounds__(DCP_THREADS, DCP_MINB) DCP_KNAME(const DcpStParams p) {
   T sc[DCP_ARR(DCP_NSCALAR)];
 #pragma unroll
   for (int i = 0; i < DCP_NSCALAR; ++i) sc[i] = p.sc[i][0];
@@ -359,7 +364,7 @@ struct DcpBatchParams {
   unsigned long long* guard;  // first launch of a deferred run: largest |input| seen
 };
 
-extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
+extern "C" __global__ void __launch_bounds__(DCP_THREADS, DCP_MINB) DCP_KNAME(const DcpBatchParams p) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;

@@ -812,7 +812,13 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
     if (d <= S && stream_eligible(G, d))
       for (int pf : {1, 2}) {
         if (G.kind == GroupKind::Batch) {
-          for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf, 1});
+          // last slot: CTAs per SM the register budget must allow (more
+          // resident warps to hide the row loads' latency, fewer registers)
+          for (int seg : {32, 64, 128}) {
+            c.push_back({d, -1, seg, pf, 1});
+            if ((d == 4 || d == 5) && pf == 1 && seg >= 64)
+              for (int minb : {12, 16}) c.push_back({d, -1, seg, pf, minb});
+          }
         } else {
           c.push_back({d, -1, 0, pf, 1});
           // small arrays: short row segments spread the strips over more warps
@@ -837,6 +843,7 @@ void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
     auto th = g.options.find(DCP_OPT_STREAM_THREADS);
     G.threads = th == g.options.end() ? 64 : (int)th->second;
     G.prefetch = cfg[3] > 0 ? cfg[3] : 1;
+    G.min_ctas = cfg[4] > 1 ? cfg[4] : 0;
     if (G.kind == GroupKind::Batch) {
       G.seg = cfg[2] > 0 ? cfg[2] : 64;
     } else {

@@ -280,7 +280,8 @@ dcp_status dcp_reduce_noalloc(const void* in, int64_t n, int32_t dtype, int32_t 
  * each timed with CUDA events on `cuda_stream` after a shorter warm-up
  * launch, and the best rate is returned.
  *   op     0 = fused multiply-add, 1 = add, 2 = multiply, 3 = add issued as
- *          a fused multiply-add by a run-time 1.0 (binary64)
+ *          a fused multiply-add by a run-time 1.0 held in one register for
+ *          all chains, 4 = the same with a register of 1.0 per chain (binary64)
  *   iters  1 .. 2^24 operations per chain (8192 runs for tens of ms on GB300)
  *   gops   receives 10^9 lane operations per second (a fused multiply-add
  *          counts once here; it is 2 flops)

@@ -22,6 +22,9 @@ constexpr int kChains = 8;
 // passes (never in practice), which keeps the arithmetic live without
 // writing device memory the caller would have to provide.
 static __device__ double dcp_probe_sink[kChains];
+// 1.0 in device memory, one per chain: values the compiler cannot see, so
+// each chain's multiplier is a register of its own (op 4)
+static __device__ double dcp_probe_ones[16] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 template <int OP, int CHAINS>
 __global__ void __launch_bounds__(kThreads) fp64_probe_kernel(long long iters, double b, double c,
@@ -33,7 +36,7 @@ __global__ void __launch_bounds__(kThreads) fp64_probe_kernel(long long iters, d
 #pragma unroll
   for (int k = 0; k < CHAINS; ++k) {
     a[k] = (double)(threadIdx.x + k) * 1e-3;
-    bb[k] = b - k * 1e-9;
+    bb[k] = OP == 4 ? dcp_probe_ones[k] : b - k * 1e-9;
     cc[k] = c + k * 1e-9;
   }
   for (long long i = 0; i < iters; ++i) {
@@ -42,7 +45,8 @@ __global__ void __launch_bounds__(kThreads) fp64_probe_kernel(long long iters, d
       if (OP == 0) a[k] = __fma_rn(a[k], bb[k], cc[k]);
       else if (OP == 1) a[k] = __dadd_rn(a[k], cc[k]);
       else if (OP == 2) a[k] = __dmul_rn(a[k], bb[k]);
-      else a[k] = __fma_rn(a[k], b, cc[k]);  // an add issued as a fused multiply-add by b = 1
+      else if (OP == 3) a[k] = __fma_rn(a[k], b, cc[k]);  // an add as a fused multiply-add by b = 1
+      else a[k] = __fma_rn(a[k], bb[k], cc[k]);  // the same, each chain with its own 1.0
     }
   }
 #pragma unroll
@@ -101,15 +105,17 @@ extern "C" dcp_status dcp_probe_fp64(int32_t op, int64_t iters, double* gops, do
                                      void* cuda_stream) {
   try {
     if (!gops) dcp::fail(DCP_E_INVALID_ARG, "gops is NULL");
-    if (op < 0 || op > 3)
-      dcp::fail(DCP_E_INVALID_ARG, "op must be 0 (fma), 1 (add), 2 (mul) or 3 (add as fma by 1)");
+    if (op < 0 || op > 4)
+      dcp::fail(DCP_E_INVALID_ARG,
+                "op must be 0 (fma), 1 (add), 2 (mul), 3 or 4 (add as fma by 1, shared or per chain)");
     if (iters < 1 || iters > (1ll << 24)) dcp::fail(DCP_E_INVALID_ARG, "iters must be in [1, 2^24]");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     float t = 0.f;
     double g = op == 0   ? best_rate<0>(iters, s, &t)
                : op == 1 ? best_rate<1>(iters, s, &t)
                : op == 2 ? best_rate<2>(iters, s, &t)
-                         : best_rate<3>(iters, s, &t);
+               : op == 3 ? best_rate<3>(iters, s, &t)
+                         : best_rate<4>(iters, s, &t);
     if (!(g > 0.0)) dcp::fail(DCP_E_CUDA, "FP64 probe timed at zero");
     *gops = g;
     if (ms) *ms = t;

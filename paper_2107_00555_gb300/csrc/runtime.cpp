@@ -814,11 +814,7 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
         if (G.kind == GroupKind::Batch) {
           // last slot: CTAs per SM the register budget must allow (more
           // resident warps to hide the row loads' latency, fewer registers)
-          for (int seg : {32, 64, 128}) {
-            c.push_back({d, -1, seg, pf, 1});
-            if ((d == 4 || d == 5) && pf == 1 && seg >= 64)
-              for (int minb : {12, 16}) c.push_back({d, -1, seg, pf, minb});
-          }
+          for (int seg : {32, 64, 128}) c.push_back({d, -1, seg, pf, 1});
         } else {
           c.push_back({d, -1, 0, pf, 1});
           // small arrays: short row segments spread the strips over more warps
@@ -1113,7 +1109,8 @@ std::string describe_plan(const GraphImpl& g) {
     if (G.kind == GroupKind::Stencil && G.shape.size() == 3) os << ", \"cells_per_thread\": " << G.cx;
     if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce)
       os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
-         << ", \"prefetch\": " << G.prefetch;
+         << ", \"prefetch\": " << G.prefetch << ", \"threads\": " << G.threads
+         << ", \"min_ctas\": " << G.min_ctas;
     int epi = 0;
     for (const StepDesc& s : G.steps) epi += (int)s.epi.size();
     os << ", \"epilogue_ops\": " << epi << "}";

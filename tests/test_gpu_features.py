@@ -412,10 +412,10 @@ def test_fp64_probe_reports_a_plausible_rate():
     torch.cuda.init()
     s = torch.cuda.current_stream().cuda_stream
     cap = 152 * 128 * 2.1
-    for op in (0, 1, 2, 3):
+    for op in (0, 1, 2, 3, 4):
         g, ms = C.dcp_probe_fp64(op, 1024, s)
         assert 0 < g < cap and ms > 0, (op, g, ms)
     with pytest.raises(C.DcpError):
-        C.dcp_probe_fp64(4, 1024, s)
+        C.dcp_probe_fp64(5, 1024, s)
     with pytest.raises(C.DcpError):
         C.dcp_probe_fp64(0, 0, s)

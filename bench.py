@@ -178,9 +178,12 @@ class MapReduce(Workload):
         # count, so the f64 line reports how busy the FP64 pipe is (the FP64
         # instructions per element that ncu counted on this exact kernel,
         # recorded in profiles/, over the probe's rate) and the HBM fraction
+        # (a sharded rank's map kernel reads its own block)
+        n = getattr(self, "roof_elements", self.n)
+        nbytes = 3 * n * (4 if self.dtype == "f32" else 8)
         if self.dtype == "f64":
-            return {"bound": "alu_issue", "hbm_bytes": self.bytes, "elements": self.n}
-        return {"bound": "hbm", "bytes": self.bytes}
+            return {"bound": "alu_issue", "hbm_bytes": nbytes, "elements": n}
+        return {"bound": "hbm", "bytes": nbytes}
 
     def describe(self):
         return {"workload": "fused map+reduce: y = exp(a*x+b)*sin(x) - 0.5*x*x; sum(y), max|y|",
@@ -284,6 +287,10 @@ class MapReduce(Workload):
         self.sm = shard.ShardedMapReduce(self.n, world, rank, local_run, combine, dist)
         self.kernels = [l["kernel"] for l in self.g.plan()["launches"]]
         self.n_launch = len(self.kernels) + 2
+        # roofline of the block's map kernel: the step is that launch plus two
+        # one-CTA combines and an all-gather of a few bytes
+        self.roof_elements = hi - lo
+        self.roof_launches = 1
         self.legs = lambda: []
         self.step = self.sm.run
         self.setup_e2e = self._setup_e2e_sharded
@@ -601,7 +608,8 @@ class Stencil(Workload):
             calls[(k, handle[id(src)])]()
 
         it = iter(bufs)
-        self.ss = shard.ShardedStencil(plan, advance, lambda: next(it), dist, backend="nccl")
+        self.ss = shard.ShardedStencil(plan, advance, lambda: next(it), dist,
+                                       backend=dist.get_backend())
         g0 = self.local_graphs[plan.chunks[0].steps]
         plan0 = g0.plan()
         self.kernels = [l["kernel"] for l in plan0["launches"]]
@@ -1048,12 +1056,18 @@ def run_dcp(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # one rank per GPU; more ranks than GPUs share them (gloo only: NCCL
+    # takes one rank per device)
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        if args.dist_backend == "nccl":
+            dist.init_process_group("nccl", device_id=dev)
+        else:
+            dist.init_process_group(args.dist_backend)
     wl = make_workload(args.workload, args.n)
     sharded = world > 1 and getattr(wl, "shardable", False)
     if sharded:
@@ -1104,7 +1118,7 @@ def run_dcp(args):
     # per-step device times: the dominant kernel's average launch duration
     # inside a step, and the median with its 95 % interval
     times = _step_times(torch, wl.step, max(10, min(args.steps, 30)), stream)
-    per_launch = statistics.mean(times) / max(1, wl.n_launch)
+    per_launch = statistics.mean(times) / max(1, getattr(wl, "roof_launches", wl.n_launch))
     med, lo, hi = median_ci95(times)
     if args.quick:
         if rank == 0:
@@ -1256,11 +1270,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dcp", choices=["dcp", "reference"])
     ap.add_argument("--workload", default="heat3d")
-    ap.add_argument("--n", type=int, default=None, help="element count override (profiling)")
+    ap.add_argument("--n", "--size", dest="n", type=int, default=None,
+                    help="element count or grid side override (profiling; --size under torchrun, "
+                         "whose own options --n abbreviates)")
     ap.add_argument("--quick", action="store_true",
                     help="time the fused program only (no comparison legs); for profiling")
     ap.add_argument("--probe", action="store_true",
                     help="measure the FP64 rate (fma, add, mul) with clocks sampled, and exit")
+    ap.add_argument("--dist-backend", default="nccl", choices=["nccl", "gloo"],
+                    help="process group under torchrun (gloo moves halos and partials through "
+                         "host memory; it lets several ranks share one GPU)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -244,6 +244,15 @@ template <typename T> struct DcpStParamsT {
   unsigned long long* guard;  // first launch of a deferred run: largest |input| seen
 };
 
+// The generated stencil sums take their multipliers from registers loaded
+// once per thread from the kernel's table dcp_km (DCP_NK entries; values the
+// compiler cannot fold into immediates, so each stays a register of its own).
+template <typename T, int N>
+__device__ __forceinline__ void dcp_load_multipliers(T (&km)[N], const double* tab) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) km[k] = (T)tab[k];
+}
+
 // Bit pattern of an element type (column masks of the warp-stream kernels).
 template <typename T> struct DcpBits { typedef unsigned type; };
 template <> struct DcpBits<double> { typedef unsigned long long type; };

@@ -17,7 +17,8 @@
 // DCP_NLOAD, DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED,
 // dcp_red_op(r) and the functions
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)  (prologue)
-//   T    dcp_sum<S>(const T* A, int c)   weighted sum of step S at tile cell c
+//   T    dcp_sum<S>(const T* A, int c, const T (&km)[DCP_NK])   weighted sum of step S
+//        at tile cell c (km: its multipliers, see dcp_load_multipliers)
 //   T    dcp_epi<S>(T v)                 epilogue maps fused after step S
 //   void dcp_post(const DcpStParams& p, const T* sc, long long i, T v, T* st, T* rv)
 typedef DCP_T T;
@@ -51,7 +52,8 @@ __device__ __forceinline__ int dcp_wrap(int q, int n) {
 // the checked path, one cell per work item.
 template <int S>
 __device__ __forceinline__ void dcp_run_step(const T* __restrict__ A, T* __restrict__ B, int y0,
-                                             int x0, int ny, int nx) {
+                                             int x0, int ny, int nx,
+                                             const T (&km)[DCP_NK]) {
   constexpr int my = (S + 1) * DCP_RY, mx = (S + 1) * DCP_RX;
   constexpr int RH = DCP_PH - 2 * my, RW = DCP_PW - 2 * mx;
   constexpr int R = (RH % 4 == 0) ? 4 : ((RH % 2 == 0) ? 2 : 1);
@@ -71,7 +73,7 @@ __device__ __forceinline__ void dcp_run_step(const T* __restrict__ A, T* __restr
       const int c0 = (my + rb * R) * DCP_PW + lx;
       T v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = dcp_sum<S>(A, c0 + r * DCP_PW);
+      for (int r = 0; r < R; ++r) v[r] = dcp_sum<S>(A, c0 + r * DCP_PW, km);
 #pragma unroll
       for (int r = 0; r < R; ++r) B[c0 + r * DCP_PW] = dcp_epi<S>(v[r]);
     }
@@ -89,21 +91,22 @@ __device__ __forceinline__ void dcp_run_step(const T* __restrict__ A, T* __restr
                (gy < DCP_RY || gy >= ny - DCP_RY || gx < DCP_RX || gx >= nx - DCP_RX)) {
       v = dcp_epi<S>(A[c]);  // ring cell keeps its value; the step's epilogue still applies
     } else {
-      v = dcp_epi<S>(dcp_sum<S>(A, c));
+      v = dcp_epi<S>(dcp_sum<S>(A, c, km));
     }
     B[c] = v;
   }
 }
 
 template <int S>
-__device__ __forceinline__ void dcp_steps(T*& A, T*& B, int y0, int x0, int ny, int nx) {
+__device__ __forceinline__ void dcp_steps(T*& A, T*& B, int y0, int x0, int ny, int nx,
+                                          const T (&km)[DCP_NK]) {
   if constexpr (S < DCP_NSTEPS) {
-    dcp_run_step<S>(A, B, y0, x0, ny, nx);
+    dcp_run_step<S>(A, B, y0, x0, ny, nx, km);
     __syncthreads();
     T* t = A;
     A = B;
     B = t;
-    dcp_steps<S + 1>(A, B, y0, x0, ny, nx);
+    dcp_steps<S + 1>(A, B, y0, x0, ny, nx, km);
   }
 }
 
@@ -112,7 +115,7 @@ __device__ __forceinline__ void dcp_steps(T*& A, T*& B, int y0, int x0, int ny, 
 // holds the tile after DCP_NSTEPS steps.
 template <class Input>
 __device__ __forceinline__ void dcp_tile(T*& A, T*& B, int ny, int nx, int tyi, int txi,
-                                         Input input) {
+                                         const T (&km)[DCP_NK], Input input) {
   const int y0 = tyi * DCP_TY - DCP_HY, x0 = txi * DCP_TX - DCP_HX;
   for (int i = threadIdx.x; i < DCP_TILE_ELEMS; i += DCP_THREADS) {
     const int ly = i / DCP_PW, lx = i - ly * DCP_PW;
@@ -129,7 +132,7 @@ __device__ __forceinline__ void dcp_tile(T*& A, T*& B, int ny, int nx, int tyi, 
     A[i] = v;
   }
   __syncthreads();
-  dcp_steps<0>(A, B, y0, x0, ny, nx);
+  dcp_steps<0>(A, B, y0, x0, ny, nx, km);
 }
 
 #if !DCP_BATCH
@@ -143,7 +146,9 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   const int ny = p.ny, nx = p.nx;
   const int tyi = blockIdx.x / p.tiles_x, txi = blockIdx.x - tyi * p.tiles_x;
   DcpGuard guard;
-  dcp_tile(A, B, ny, nx, tyi, txi, [&](long long gi) {
+  T km[DCP_NK];
+  dcp_load_multipliers(km, dcp_km);
+  dcp_tile(A, B, ny, nx, tyi, txi, km, [&](long long gi) {
     const T v = dcp_input(p, sc, gi);
     if (DCP_GUARD) guard.see(v);
     return v;
@@ -202,6 +207,8 @@ struct DcpBatchParams {
 extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBatchParams p) {
   extern __shared__ __align__(16) unsigned char dcp_smem[];
   DcpGuard guard;
+  T km[DCP_NK];
+  dcp_load_multipliers(km, dcp_km);
   for (int w = blockIdx.x; w < p.total_tiles; w += gridDim.x) {
     int lo = 0, hi = p.ninst - 1;
     while (lo < hi) {
@@ -215,7 +222,7 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpBat
     T* A = reinterpret_cast<T*>(dcp_smem);
     T* B = A + DCP_TILE_ELEMS;
     const T* in = I.in;
-    dcp_tile(A, B, I.ny, I.nx, tyi, txi, [&](long long gi) {
+    dcp_tile(A, B, I.ny, I.nx, tyi, txi, km, [&](long long gi) {
       const T v = in[gi];
       if (DCP_GUARD) guard.see(v);
       return v;

@@ -21,7 +21,8 @@
 // DCP_NSTORE, DCP_NRED, DCP_NSCALAR, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)   (prologue)
 //   void dcp_level<L>(const T (&up)[NR][C], const T (&lf)[NR][RX], const T (&rt)[NR][RX],
-//                     T (&out)[C])   weighted sum of step L (rows up[RY+dy]),
+//                     T (&out)[C], const T (&km)[DCP_NK])   weighted sum of step L
+//                     (rows up[RY+dy]; km: its multipliers, see dcp_load_multipliers),
 //   T    dcp_epi<L>(T v)                 epilogue maps fused after step L
 //   bool dcp_uses_lf(int L, int d), dcp_uses_rt(int L, int d)   (constexpr)
 //        whether step L reads a left / right neighbour column in row d
@@ -64,6 +65,7 @@ struct DcpItem {
 struct DcpCols {
   int col0;
   typename DcpBits<T>::type keep[C];
+  T km[DCP_NK];  // multipliers of the sums (see dcp_load_multipliers)
 };
 
 // CHECK: the strip reaches outside the array (per-column tests).  ROWS: every
@@ -98,7 +100,7 @@ __device__ __forceinline__ void dcp_level_step(T (&ring)[K > 1 ? K : 1][NR][C], 
       if (dcp_uses_rt(L - 1, d)) rt[d][q] = __shfl_down_sync(0xffffffffu, up[d][q], 1);
     }
   T v[C];
-  dcp_level<L - 1>(up, lf, rt, v);
+  dcp_level<L - 1>(up, lf, rt, v, cols.km);
   const bool row_in = ROWS || (unsigned)y < (unsigned)it.ny;
   if (!CHECK) {
     // every column of the strip lies inside the array (and outside a fixed
@@ -240,9 +242,11 @@ __device__ __forceinline__ void dcp_prefill(T (&q)[PD][C], int j0, const DcpItem
 
 template <bool CHECK, class Input, class Output>
 __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input, Output& output,
-                                                DcpGuard& guard) {
+                                                DcpGuard& guard, const T (&km)[DCP_NK]) {
   const int lane = threadIdx.x & 31;
   DcpCols cols;
+#pragma unroll
+  for (int k = 0; k < DCP_NK; ++k) cols.km[k] = km[k];
   cols.col0 = it.x0 - K * DCP_RX + lane * C;
 #pragma unroll
   for (int c = 0; c < C; ++c)
@@ -285,13 +289,13 @@ __device__ __forceinline__ void dcp_stream_impl(const DcpItem& it, Input& input,
 // With DCP_GUARD every row the stream reads enters the magnitude guard.
 template <class Input, class Output>
 __device__ __forceinline__ void dcp_stream(const DcpItem& it, Input&& input, DcpGuard& guard,
-                                           Output&& output) {
+                                           const T (&km)[DCP_NK], Output&& output) {
   const int lo = DCP_BC == DCP_BC_FIXED_RING ? DCP_RX : 0;
   const int first = it.x0 - K * DCP_RX;
   if (first >= lo && first + SPAN <= it.nx - lo)
-    dcp_stream_impl<false>(it, input, output, guard);
+    dcp_stream_impl<false>(it, input, output, guard, km);
   else
-    dcp_stream_impl<true>(it, input, output, guard);
+    dcp_stream_impl<true>(it, input, output, guard, km);
 }
 
 #if !DCP_BATCH
@@ -312,13 +316,15 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS, DCP_MINB) DCP_KNAME(co
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
   DcpGuard guard;
+  T km[DCP_NK];
+  dcp_load_multipliers(km, dcp_km);
   for (int w = warp; w < items; w += nwarps) {
     const int sg = w / strips, st = w - sg * strips;
     DcpItem it{nullptr, nullptr, ny, nx, st * W, sg * SEG, min(ny, (sg + 1) * SEG)};
     const int col0 = it.x0 - K * DCP_RX + lane * C;
     dcp_stream(
         it,
-        [&](long long gi) { return dcp_input(p, sc, gi); }, guard,
+        [&](long long gi) { return dcp_input(p, sc, gi); }, guard, km,
         [&](int y, const T (&v)[C]) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {
@@ -369,6 +375,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS, DCP_MINB) DCP_KNAME(co
   const int warp = (blockIdx.x * DCP_THREADS + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * DCP_THREADS) >> 5;
   DcpGuard guard;
+  T km[DCP_NK];
+  dcp_load_multipliers(km, dcp_km);
   for (int w = warp; w < p.total_tiles; w += nwarps) {
     int lo = 0, hi = p.ninst - 1;
     while (lo < hi) {
@@ -385,7 +393,7 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS, DCP_MINB) DCP_KNAME(co
     const int col0 = it.x0 - K * DCP_RX + lane * C;
     dcp_stream(
         it,
-        [&](long long gi) { return in[gi]; }, guard,
+        [&](long long gi) { return in[gi]; }, guard, km,
         [&](int y, const T (&v)[C]) {
 #pragma unroll
           for (int c = 0; c < C; ++c) {

@@ -19,7 +19,8 @@
 // DCP_RY, DCP_RZ, DCP_CX, DCP_AX, DCP_BC, DCP_THREADS, DCP_KNAME, DCP_LAST, DCP_GUARD,
 // DCP_NLOAD, DCP_NPLOAD, DCP_NSTORE, DCP_NSCALAR, DCP_NRED, dcp_red_op(r) and
 //   T    dcp_input(const DcpStParams& p, const T* sc, long long i)
-//   void dcp_sum3(const T* const* pl, int c, T (&v)[DCP_CX])
+//   void dcp_sum3(const T* const* pl, int c, T (&v)[DCP_CX], const T (&km)[DCP_NK])
+//        (km: the multipliers of the sum, see dcp_load_multipliers)
 //        weighted sums of cells c .. c+CX-1 of the plane ring; pl[dz + RZ] = plane z + dz
 //   T    dcp_epi3(T v)                         epilogue maps fused after the step
 //   void dcp_post(const DcpStParams& p, const T* sc, long long i, T v, T* st, T* rv)
@@ -87,6 +88,8 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
   T sc[DCP_ARR(DCP_NSCALAR)];
 #pragma unroll
   for (int i = 0; i < DCP_NSCALAR; ++i) sc[i] = p.sc[i][0];
+  T km[DCP_NK];
+  dcp_load_multipliers(km, dcp_km);
   const int nz = p.nz, ny = p.ny, nx = p.nx;
   const int tyi = blockIdx.x / p.tiles_x, txi = blockIdx.x - tyi * p.tiles_x;
   const int y0 = tyi * DCP_TY - DCP_RY, x0 = txi * DCP_TX - DCP_RX;
@@ -140,7 +143,7 @@ extern "C" __global__ void __launch_bounds__(DCP_THREADS) DCP_KNAME(const DcpStP
       if (gy >= ny || gx >= nx) continue;
       const int c = (ty + DCP_RY) * DCP_PW + tx + DCP_AX;
       T v[DCP_CX];
-      dcp_sum3(pl, c, v);
+      dcp_sum3(pl, c, v, km);
 #pragma unroll
       for (int j = 0; j < DCP_CX; ++j) {
         if (j > 0 && gx + j >= nx) break;

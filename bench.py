@@ -576,7 +576,7 @@ class Stencil(Workload):
         return self.name == "heat3d"
 
     def shard_desc(self, world):
-        from paper_2107_00555_gb300 import programs, shard
+        from paper_2107_00555_gb300 import shard
         plan = shard.SlabPlan(self.shape, 1, self.bc, self.T, world, 0, self.shard_depth)
         return plan.describe()
 

@@ -124,8 +124,12 @@ enum {
   DCP_OPT_MAP_UNROLL = 14,      /* map kernels: 16-byte vectors per array in flight per thread (1..8) */
   DCP_OPT_DEFERRED_WEIGHT = 15, /* stencils: 1 (default) deferred common weight where it applies,
                                    0 the plain weighted sum everywhere (set before dcp_fuse) */
-  DCP_OPT_STREAM_MIN_CTAS = 16  /* warp-stream stencils: CTAs per SM the register budget must
+  DCP_OPT_STREAM_MIN_CTAS = 16, /* warp-stream stencils: CTAs per SM the register budget must
                                    allow (1..32; default: the compiler's choice) */
+  DCP_OPT_ADJOINT_DEPTH = 17    /* reverse pass of 1-D / 2-D stencil chains with step
+                                   epilogues: k >= 1 runs k reverse steps per launch from every
+                                   k-th state, recomputing the forward states in the tile; 0
+                                   (default) one launch per step (0..64; set before dcp_fuse) */
 };
 
 /* ---- graph construction ------------------------------------------------ */
@@ -235,6 +239,13 @@ dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const
  * not fit).  Asynchronous on `cuda_stream`. */
 dcp_status dcp_run_adjoint(dcp_graph g, const void* const* inputs, const void* const* out_grads,
                            void* const* in_grads, size_t tape_budget_bytes, void* cuda_stream);
+
+/* Plans the reverse pass for `tape_budget_bytes` and compiles its kernels
+ * without running it (no GPU needed; the paper compiles a program once and
+ * then calls it, Sec. 2.4).  dcp_plan_info then lists the reverse pass's
+ * launches; a later dcp_run_adjoint with the same budget reuses the plan.
+ * DCP_E_OOM when even sqrt(T) checkpointing exceeds the budget. */
+dcp_status dcp_prepare_adjoint(dcp_graph g, size_t tape_budget_bytes);
 
 /* Waits for `cuda_stream` and reports asynchronous CUDA errors, and
  * DCP_E_UNSUPPORTED when a deferred common-weight run of the last dcp_run

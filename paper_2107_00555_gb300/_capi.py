@@ -54,6 +54,7 @@ DCP_OPT_CELLS_PER_THREAD = 13
 DCP_OPT_MAP_UNROLL = 14
 DCP_OPT_DEFERRED_WEIGHT = 15
 DCP_OPT_STREAM_MIN_CTAS = 16
+DCP_OPT_ADJOINT_DEPTH = 17
 
 _STATUS_NAMES = {v: k for k, v in globals().items() if k.startswith("DCP_E_") or k == "DCP_OK"}
 
@@ -94,6 +95,7 @@ _SIG = [
     ("dcp_run_host", ctypes.c_int32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
     ("dcp_run_adjoint", ctypes.c_int32, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), ctypes.c_size_t, _P]),
+    ("dcp_prepare_adjoint", ctypes.c_int32, [_P, ctypes.c_size_t]),
     ("dcp_sync", ctypes.c_int32, [_P, _P]),
     ("dcp_set_option", ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64]),
     ("dcp_plan_info", ctypes.c_int32, [_P, ctypes.c_char_p, ctypes.c_size_t,
@@ -211,6 +213,10 @@ def dcp_run_adjoint(g, inputs, out_grads, in_grads, tape_budget_bytes, stream=0)
     _check("dcp_run_adjoint", load().dcp_run_adjoint(g, _ptrs(inputs), _ptrs(out_grads),
                                                      _ptrs(in_grads), int(tape_budget_bytes),
                                                      stream))
+
+
+def dcp_prepare_adjoint(g, tape_budget_bytes):
+    _check("dcp_prepare_adjoint", load().dcp_prepare_adjoint(g, int(tape_budget_bytes)))
 
 
 def dcp_sync(g, stream=0):

@@ -163,6 +163,121 @@ struct ReverseBuilder {
     R = sub.g.get();
   }
 
+  // A chain of 1-D / 2-D one-step stencil nodes u_{i+1} = E_i(S_i u_i)
+  // (E_i: the unary / immediate maps following S_i) inside this segment,
+  // every intermediate read only by the next node.  Its reverse runs as
+  // time-tiled chunks (AdjChain nodes) that recompute the forward states
+  // inside each tile from every K-th state.
+  struct Chain {
+    std::vector<int> st;                // stencil nodes, in order
+    std::vector<std::vector<int>> epi;  // epilogue map nodes of each
+    int in = -1;                        // u_0
+    int last = -1;                      // node whose value is the chain's result
+    int K = 0;                          // reverse steps per launch
+  };
+  std::map<int, Chain> chains;  // keyed by `last`
+
+  bool single_internal_user(int v, int& u) const {
+    if (P.is_out[v] || P.users[v].size() != 1) return false;
+    u = P.users[v][0];
+    return u < n1;
+  }
+
+  bool chain_stencil(int v, const Node& like) const {
+    const Node& n = F.nodes[v];
+    return n.kind == Kind::Stencil && n.steps == 1 && n.ndim() >= 1 && n.ndim() <= 2 &&
+           (n.bc == DCP_BC_ZERO || n.bc == DCP_BC_PERIODIC) && n.dtype == like.dtype &&
+           n.shape == like.shape && n.bc == like.bc && n.offsets == like.offsets;
+  }
+
+  static bool epilogue_op(int op) {
+    switch (op) {
+      case DCP_NEG: case DCP_ABS: case DCP_EXP: case DCP_SIN: case DCP_COS: case DCP_TANH:
+      case DCP_SQRT: case DCP_SQUARE: case DCP_ADD_S: case DCP_SUB_S: case DCP_MUL_S:
+      case DCP_RSUB_S: return true;
+    }
+    return false;
+  }
+
+  void find_chains() {
+    auto it = F.options.find(DCP_OPT_ADJOINT_DEPTH);
+    std::set<int> seen;
+    for (int v = n0; v < n1; ++v) {
+      const Node& head = F.nodes[v];
+      if (seen.count(v) || !chain_stencil(v, head)) continue;
+      // reverse steps per launch (DCP_OPT_ADJOINT_DEPTH; default off: the
+      // recomputation trades device-memory traffic and tape for FP32 / FP64
+      // work, which pays only where memory bounds the per-step reverse)
+      const int64_t K = it != F.options.end() ? it->second : 0;
+      if (K < 1) continue;
+      Chain c;
+      c.in = head.in[0];
+      c.K = (int)K;
+      int s = v;
+      for (;;) {
+        seen.insert(s);
+        c.st.push_back(s);
+        c.epi.emplace_back();
+        int x = s, u = -1;
+        while (single_internal_user(x, u)) {
+          const Node& m = F.nodes[u];
+          if (m.kind != Kind::Map || !epilogue_op(m.op) || m.shape != head.shape ||
+              m.dtype != head.dtype)
+            break;
+          c.epi.back().push_back(u);
+          x = u;
+        }
+        c.last = x;
+        if (!single_internal_user(x, u) || !chain_stencil(u, head)) break;
+        s = u;
+      }
+      // worth it only where a step before the last has an epilogue (a chain
+      // that is linear up to its last step reverses as a transposed stencil
+      // chain, time tiled as such); binary64 steps without an epilogue may
+      // run on a deferred common weight in the forward pass, which the
+      // recomputation does not reproduce
+      bool nonlinear = false, all_epi = true;
+      for (size_t i = 0; i < c.epi.size(); ++i) {
+        nonlinear = nonlinear || (i + 1 < c.epi.size() && !c.epi[i].empty());
+        all_epi = all_epi && !c.epi[i].empty();
+      }
+      if (!nonlinear || (head.dtype == DCP_F64 && !all_epi)) continue;
+      chains[c.last] = c;
+    }
+  }
+
+  // Reverse of chain c, given the cotangent `a` of its result: chunks of K
+  // steps from the end; each reads its first state (input or tape) and the
+  // cotangent of its last, and yields the cotangent of its first.
+  void chain_vjp(const Chain& c, int a) {
+    const Node& head = F.nodes[c.st[0]];
+    const int K = c.K;
+    const int m = (int)c.st.size();
+    int cot_v = full(a, head.shape);
+    for (int b = m; b > 0;) {
+      const int s0 = ((b - 1) / K) * K;  // chunks start at multiples of K
+      const int ua = s0 == 0 ? c.in : (c.epi[s0 - 1].empty() ? c.st[s0 - 1] : c.epi[s0 - 1].back());
+      Node n;
+      n.kind = Kind::AdjChain;
+      n.dtype = head.dtype;
+      n.shape = head.shape;
+      n.bc = head.bc;
+      n.offsets = head.offsets;
+      n.weights = head.weights;
+      n.steps = b - s0;
+      for (int i = s0; i < b; ++i) {
+        AdjStep st;
+        st.weights = F.nodes[c.st[i]].weights;
+        for (int e : c.epi[i]) st.epi.emplace_back(F.nodes[e].op, F.nodes[e].imm);
+        n.chain.push_back(st);
+      }
+      n.in = {fwd_value(ua), cot_v};
+      cot_v = b_node(*R, std::move(n));
+      b = s0;
+    }
+    acc(c.in, cot_v);
+  }
+
   int fwd_value(int v) {
     auto it = fwd.find(v);
     if (it != fwd.end()) return it->second;
@@ -256,6 +371,7 @@ struct ReverseBuilder {
   }
 
   void build(std::map<int, int>& ver) {
+    find_chains();
     // seeds: cotangents of values of this segment that are outputs or read later
     for (int v = n0; v < n1; ++v) {
       const Node& n = F.nodes[v];
@@ -286,7 +402,13 @@ struct ReverseBuilder {
       if (it == cot.end()) continue;
       const Node& n = F.nodes[v];
       int a = it->second;
+      auto ch = chains.find(v);
+      if (ch != chains.end()) {
+        chain_vjp(ch->second, a);
+        continue;
+      }
       switch (n.kind) {
+        case Kind::AdjChain:
         case Kind::Input: break;
         case Kind::Map: map_vjp(v, a); break;
         case Kind::Stencil:
@@ -554,27 +676,32 @@ static void fuse_sub(Sub& s, uint32_t flags, const std::map<int, int64_t>& optio
   s.g->fused = true;
 }
 
+// Plans the reverse pass for `budget` and compiles its kernels (no device
+// work); a plan for the same budget is kept.
+void prepare_adjoint_impl(GraphImpl& g, AdjointState& st, size_t budget) {
+  if (st.built && st.budget == budget) return;
+  AdjointPlan p;
+  plan_adjoint(g, budget, p);
+  fuse_sub(p.forward, g.flags, g.options);
+  for (Sub& x : p.seg_fwd) fuse_sub(x, g.flags, g.options);
+  for (Sub& x : p.seg_rev) fuse_sub(x, g.flags, g.options);
+  st.plan = std::move(p);
+  st.budget = budget;
+  st.built = true;
+  if (st.arena) {
+    cudaFree(st.arena);
+    st.allocs.erase(std::find(st.allocs.begin(), st.allocs.end(), st.arena));
+    st.arena = nullptr;
+  }
+}
+
 void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
                       const void* const* out_grads, void* const* in_grads, size_t budget,
                       cudaStream_t s) {
-  if (!st.built || st.budget != budget) {
-    AdjointPlan p;
-    plan_adjoint(g, budget, p);
-    fuse_sub(p.forward, g.flags, g.options);
-    for (Sub& x : p.seg_fwd) fuse_sub(x, g.flags, g.options);
-    for (Sub& x : p.seg_rev) fuse_sub(x, g.flags, g.options);
-    st.plan = std::move(p);
-    st.budget = budget;
-    st.built = true;
-    if (st.arena) {
-      cudaFree(st.arena);
-      st.allocs.erase(std::find(st.allocs.begin(), st.allocs.end(), st.arena));
-      st.arena = nullptr;
-    }
-    if (st.plan.arena_bytes) {
-      check_cuda(cudaMalloc(&st.arena, st.plan.arena_bytes), "cudaMalloc(adjoint tape)");
-      st.allocs.push_back(st.arena);
-    }
+  prepare_adjoint_impl(g, st, budget);
+  if (st.plan.arena_bytes && !st.arena) {
+    check_cuda(cudaMalloc(&st.arena, st.plan.arena_bytes), "cudaMalloc(adjoint tape)");
+    st.allocs.push_back(st.arena);
   }
   std::map<int, int> input_index;
   for (size_t i = 0; i < g.inputs.size(); ++i) input_index[g.inputs[i]] = (int)i;

@@ -360,6 +360,14 @@ dcp_status dcp_run_adjoint(dcp_graph gh, const void* const* inputs, const void* 
   });
 }
 
+dcp_status dcp_prepare_adjoint(dcp_graph gh, size_t tape_budget_bytes) {
+  return guarded([&] {
+    GraphImpl& g = G(gh);
+    if (!g.fused) fail(DCP_E_STATE, "call dcp_fuse before dcp_prepare_adjoint");
+    prepare_adjoint(g, tape_budget_bytes);
+  });
+}
+
 dcp_status dcp_sync(dcp_graph gh, void* cuda_stream) {
   return guarded([&] {
     GraphImpl& g = G(gh);
@@ -384,6 +392,7 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
       case DCP_OPT_MAP_UNROLL:
       case DCP_OPT_DEFERRED_WEIGHT:
       case DCP_OPT_STREAM_MIN_CTAS:
+      case DCP_OPT_ADJOINT_DEPTH:
         if (g.fused) fail(DCP_E_STATE, "tiling options must be set before dcp_fuse");
         break;
       case DCP_OPT_USE_GRAPH:
@@ -408,6 +417,7 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
     if (key == DCP_OPT_MAP_UNROLL && (v < 1 || v > 8)) fail(DCP_E_INVALID_ARG, "map unroll must be in 1..8");
     if (key == DCP_OPT_DEFERRED_WEIGHT && v != 0 && v != 1) fail(DCP_E_INVALID_ARG, "deferred weight must be 0 or 1");
     if (key == DCP_OPT_STREAM_MIN_CTAS && (v < 1 || v > 32)) fail(DCP_E_INVALID_ARG, "stream min CTAs must be in 1..32");
+    if (key == DCP_OPT_ADJOINT_DEPTH && v > 64) fail(DCP_E_INVALID_ARG, "adjoint depth must be in 0..64");
     g.options[key] = v;
   });
 }

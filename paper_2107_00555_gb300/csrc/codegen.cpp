@@ -78,12 +78,11 @@ std::string imm_literal(int dtype, double imm) {
 // Weight literal in the group's dtype (stencils are floating).
 std::string weight_literal(int dtype, double w) { return imm_literal(dtype, w); }
 
-// C expression of map node v applied to operand expressions.
-std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std::string& b) {
-  const Node& n = g.nodes[v];
-  if (n.kind == Kind::Stencil) return a;  // zero-step stencil: identity
-  std::string imm = imm_literal(n.dtype, n.imm);
-  switch (n.op) {
+// C expression of map op `op` (dtype, immediate) applied to operand
+// expressions.
+std::string op_expr(int op, int dtype, double imm_v, const std::string& a, const std::string& b) {
+  std::string imm = imm_literal(dtype, imm_v);
+  switch (op) {
     case kOpBcast: return a;
     case kOpConst: return imm;
     case kOpSign: return "dcp_sign(" + a + ")";
@@ -91,9 +90,9 @@ std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std:
     case kOpLt: return "dcp_lt(" + a + ", " + b + ")";
     case DCP_NEG: return "dcp_neg(" + a + ")";
     case DCP_ABS: return "dcp_abs(" + a + ")";
-    case DCP_EXP: return (n.dtype == DCP_F64 ? "dcp_exp64(" : "dcp_exp(") + a + ")";
-    case DCP_SIN: return (n.dtype == DCP_F64 ? "dcp_sin64(" : "dcp_sin(") + a + ")";
-    case DCP_COS: return (n.dtype == DCP_F64 ? "dcp_cos64(" : "dcp_cos(") + a + ")";
+    case DCP_EXP: return (dtype == DCP_F64 ? "dcp_exp64(" : "dcp_exp(") + a + ")";
+    case DCP_SIN: return (dtype == DCP_F64 ? "dcp_sin64(" : "dcp_sin(") + a + ")";
+    case DCP_COS: return (dtype == DCP_F64 ? "dcp_cos64(" : "dcp_cos(") + a + ")";
     case DCP_TANH: return "dcp_tanh(" + a + ")";
     case DCP_SQRT: return "dcp_sqrt(" + a + ")";
     case DCP_SQUARE: return "dcp_square(" + a + ")";
@@ -109,6 +108,13 @@ std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std:
     case DCP_RSUB_S: return "dcp_sub(" + imm + ", " + a + ")";
   }
   fail(DCP_E_INVALID_ARG, "codegen: unknown op");
+}
+
+// C expression of map node v applied to operand expressions.
+std::string map_expr(const GraphImpl& g, int v, const std::string& a, const std::string& b) {
+  const Node& n = g.nodes[v];
+  if (n.kind == Kind::Stencil) return a;  // zero-step stencil: identity
+  return op_expr(n.op, n.dtype, n.imm, a, b);
 }
 
 void emit_members(std::ostringstream& os, const GraphImpl& g, const std::vector<int>& members) {
@@ -139,7 +145,8 @@ uint64_t skeleton_hash(const std::string& body) {
       {"k_stencil3d.cuh", kernel_stencil3d_source()},
       {"k_stencil2d_stream.cuh", kernel_stream_source()},
       {"k_axis.cuh", kernel_axis_source()},
-      {"k_math64.cuh", kernel_math64_source()}};
+      {"k_math64.cuh", kernel_math64_source()},
+      {"k_stencil_adj.cuh", kernel_adj_source()}};
   for (const auto& k : skel)
     if (body.find(std::string("#include \"") + k.first + "\"") != std::string::npos) text += k.second;
   return fnv1a(text);
@@ -727,6 +734,147 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
 
 CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& G, int s0, int s1) {
   return gen_stencil_kernel(g, G, s0, s1);
+}
+
+
+// ---------------------------------------------------------------------------
+// Time-tiled reverse pass of a 1-D / 2-D stencil chain (k_stencil_adj.cuh).
+// ---------------------------------------------------------------------------
+namespace {
+
+// Which forward value the reverse rule of a unary / immediate op reads:
+// 1 its operand X, 2 its result Y, 0 neither.  The rules are those of the
+// adjoint's per-op reverse maps, so the fused reverse rounds alike.
+int vjp_reads(int op) {
+  switch (op) {
+    case DCP_ABS: case DCP_SIN: case DCP_COS: case DCP_SQUARE: return 1;
+    case DCP_EXP: case DCP_TANH: case DCP_SQRT: return 2;
+    case DCP_NEG: case DCP_ADD_S: case DCP_SUB_S: case DCP_MUL_S: case DCP_RSUB_S: return 0;
+  }
+  fail(DCP_E_UNSUPPORTED, std::string("adjoint: no reverse rule for epilogue op ") + op_name(op));
+}
+
+// Cotangent of the operand of op from the cotangent a of its result (the
+// same expressions as the per-op reverse maps of the adjoint builder).
+std::string vjp_expr(int op, double imm, int T, const std::string& a, const std::string& X,
+                     const std::string& Y) {
+  switch (op) {
+    case DCP_NEG: return op_expr(DCP_NEG, T, 0, a, "");
+    case DCP_ABS: return op_expr(DCP_MUL, T, 0, op_expr(kOpSign, T, 0, X, ""), a);
+    case DCP_EXP: return op_expr(DCP_MUL, T, 0, Y, a);
+    case DCP_SIN: return op_expr(DCP_MUL, T, 0, op_expr(DCP_COS, T, 0, X, ""), a);
+    case DCP_COS:
+      return op_expr(DCP_MUL, T, 0, op_expr(DCP_NEG, T, 0, op_expr(DCP_SIN, T, 0, X, ""), ""), a);
+    case DCP_TANH:
+      return op_expr(DCP_MUL, T, 0,
+                     op_expr(DCP_RSUB_S, T, 1.0, op_expr(DCP_SQUARE, T, 0, Y, ""), ""), a);
+    case DCP_SQRT: return op_expr(DCP_DIV, T, 0, op_expr(DCP_MUL_S, T, 0.5, a, ""), Y);
+    case DCP_SQUARE:
+      return op_expr(DCP_MUL, T, 0, op_expr(DCP_MUL_S, T, 2.0, X, ""), a);
+    case DCP_ADD_S: case DCP_SUB_S: return a;
+    case DCP_MUL_S: return op_expr(DCP_MUL_S, T, imm, a, "");
+    case DCP_RSUB_S: return op_expr(DCP_NEG, T, 0, a, "");
+  }
+  fail(DCP_E_UNSUPPORTED, std::string("adjoint: no reverse rule for epilogue op ") + op_name(op));
+}
+
+}  // namespace
+
+bool adj_needs_z(const std::vector<std::pair<int, double>>& epi) {
+  const int m = (int)epi.size();
+  for (int j = 0; j < m; ++j) {
+    const int r = vjp_reads(epi[j].first);
+    if (r == 1) return true;               // the operand: z or an intermediate
+    if (r == 2 && j + 1 < m) return true;  // an intermediate result
+  }
+  return false;
+}
+
+CodegenOut gen_adj_kernel(const GraphImpl& g, const Group& G) {
+  NameScope names;
+  const Node& n = g.nodes[G.st_out];
+  const int T = G.dtype;
+  const int K = (int)n.chain.size();
+  const int nd = (int)G.shape.size();
+  const int ry = nd == 1 ? 0 : G.radius[1], rx = G.radius[2];
+  const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
+  const int PW = TX + 4 * K * rx, PH = TY + 4 * K * ry;
+  bool needz = false;
+  for (const AdjStep& st : n.chain) needz = needz || adj_needs_z(st.epi);
+  std::ostringstream os;
+  os << "// dcp time-tiled reverse stencil kernel: " << K << " steps per launch, bc " << G.bc << ", "
+     << nd << "-D\n";
+  os << "#define DCP_T " << dtype_cname(T) << "\n#define DCP_THREADS " << G.threads
+     << "\n#define DCP_BC " << G.bc << "\n#define DCP_TX " << TX << "\n#define DCP_TY " << TY
+     << "\n#define DCP_RX " << rx << "\n#define DCP_RY " << ry << "\n#define DCP_K " << K
+     << "\n#define DCP_NEEDZ " << (needz ? 1 : 0) << "\n";
+  os << "#include \"dcp_device.cuh\"\n";
+  MulRegs km;
+  km.on = T == DCP_F64;
+  std::ostringstream fn;  // emitted after the multiplier table they use
+  for (int s = 0; s < K; ++s) {
+    const AdjStep& st = n.chain[s];
+    const int P = (int)st.weights.size();
+    for (int dir = 0; dir < 2; ++dir) {  // 0: forward sum, 1: transposed sum
+      fn << "template <> __device__ __forceinline__ DCP_T " << (dir ? "dcp_bsum<" : "dcp_fsum<") << s
+         << ">(const DCP_T* A, int c, const DCP_T (&km)[DCP_NK]) {\n  (void)km;\n";
+      for (int k = 0; k < P; ++k) {
+        const int sg = dir ? -1 : 1;
+        const int dy = sg * G.offsets[k * 3 + 1], dx = sg * G.offsets[k * 3 + 2];
+        emit_term(fn, T, "acc", "A[c + (" + std::to_string(dy * PW + dx) + ")]", st.weights[k],
+                  k == 0, false, km);
+      }
+      fn << "  return acc;\n}\n";
+    }
+    // forward epilogue
+    fn << "template <> __device__ __forceinline__ DCP_T dcp_fepi<" << s << ">(DCP_T v) {\n";
+    std::string cur = "v";
+    for (size_t j = 0; j < st.epi.size(); ++j) {
+      std::string nv = "e" + std::to_string(j);
+      fn << "  const DCP_T " << nv << " = " << op_expr(st.epi[j].first, T, st.epi[j].second, cur, "")
+         << ";\n";
+      cur = nv;
+    }
+    fn << "  return " << cur << ";\n}\n";
+    // reverse of the epilogue: intermediates recomputed from z when read
+    fn << "template <> __device__ __forceinline__ DCP_T dcp_vjp<" << s
+       << ">(DCP_T g, DCP_T z, DCP_T u) {\n  (void)z; (void)u;\n";
+    const int m = (int)st.epi.size();
+    std::vector<std::string> val(m + 1);  // val[0] = z, val[j] = result of op j-1
+    val[0] = "z";
+    const bool need = adj_needs_z(st.epi);
+    for (int j = 0; j < m; ++j) {
+      if (need && j + 1 < m) {
+        val[j + 1] = "f" + std::to_string(j);
+        fn << "  const DCP_T " << val[j + 1] << " = "
+           << op_expr(st.epi[j].first, T, st.epi[j].second, val[j], "") << ";\n";
+      }
+    }
+    if (m > 0) val[m] = "u";
+    std::string a = "g";
+    for (int j = m - 1; j >= 0; --j) {
+      std::string nv = "a" + std::to_string(j);
+      fn << "  const DCP_T " << nv << " = "
+         << vjp_expr(st.epi[j].first, st.epi[j].second, T, a, val[j], val[j + 1]) << ";\n";
+      a = nv;
+    }
+    fn << "  return " << a << ";\n}\n";
+  }
+  os << km.table();
+  os << "template <int S> __device__ __forceinline__ DCP_T dcp_fsum(const DCP_T* A, int c, const "
+        "DCP_T (&km)[DCP_NK]);\n"
+     << "template <int S> __device__ __forceinline__ DCP_T dcp_bsum(const DCP_T* A, int c, const "
+        "DCP_T (&km)[DCP_NK]);\n"
+     << "template <int S> __device__ __forceinline__ DCP_T dcp_fepi(DCP_T v);\n"
+     << "template <int S> __device__ __forceinline__ DCP_T dcp_vjp(DCP_T g, DCP_T z, DCP_T u);\n";
+  os << fn.str();
+  os << "#include \"k_stencil_adj.cuh\"\n";
+  CodegenOut out;
+  out.threads = G.threads;
+  out.smem_bytes = (K + 1 + (needz ? K : 0)) * PW * PH * dtype_size(T);
+  out.source = finish("dcp_adj", os.str());
+  out.name = kname_of(out.source);
+  return out;
 }
 
 }  // namespace dcp

@@ -50,7 +50,15 @@ const char* dtype_name(int dtype);
 // ---------------------------------------------------------------------------
 // Graph IR: one node per NumPy-level operation (SSA form, Sec. 2.3).
 // ---------------------------------------------------------------------------
-enum class Kind { Input, Map, Stencil, Reduce };
+enum class Kind { Input, Map, Stencil, Reduce, AdjChain };
+
+// One forward step of a chain whose reverse runs as one AdjChain node: the
+// step's weights (the chain's common offsets) and its epilogue maps
+// (unary / immediate ops, in order).
+struct AdjStep {
+  std::vector<double> weights;
+  std::vector<std::pair<int, double>> epi;  // (op, imm)
+};
 
 struct Node {
   Kind kind = Kind::Input;
@@ -66,6 +74,10 @@ struct Node {
   int steps = 0;
   // reduce: the reduced axis of the operand, -1 = all axes
   int axis = -1;
+  // AdjChain (built by the adjoint only): in = {u_t, cotangent of u_{t+k}},
+  // value = cotangent of u_t through the k = chain.size() forward steps
+  // u_{i+1} = E_i(S_i u_i) (1-D / 2-D, offsets/bc/shape as for a stencil)
+  std::vector<AdjStep> chain;
   int64_t numel() const {
     int64_t n = 1;
     for (auto s : shape) n *= s;
@@ -93,7 +105,7 @@ const char* red_name(int red);
 // Fused plan (Sec. 3.1: greedy subgraph fusion, tiled write-conflict
 // resolution, transient mitigation).
 // ---------------------------------------------------------------------------
-enum class GroupKind { Map, Stencil, Batch, AxisReduce };
+enum class GroupKind { Map, Stencil, Batch, AxisReduce, AdjTile };
 
 // One step of an iterated stencil inside a stencil group.  `node` is the
 // stencil node providing offsets/weights; `epi` the unary/immediate map nodes
@@ -172,6 +184,7 @@ const char* kernel_stencil3d_source();  // k_stencil3d.cuh
 const char* kernel_stream_source();     // k_stencil2d_stream.cuh
 const char* kernel_axis_source();       // k_axis.cuh
 const char* kernel_math64_source();     // k_math64.cuh
+const char* kernel_adj_source();        // k_stencil_adj.cuh
 
 // ---------------------------------------------------------------------------
 // Graph object
@@ -206,10 +219,12 @@ void run_graph_host(GraphImpl& g, const void* const* inputs, void* const* output
                     cudaStream_t s);
 void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out_grads,
                  void* const* in_grads, size_t budget, cudaStream_t s);
+void prepare_adjoint(GraphImpl& g, size_t budget);
 void sync_graph(GraphImpl& g, cudaStream_t s);
 void run_adjoint_impl(GraphImpl& g, AdjointState& st, const void* const* inputs,
                       const void* const* out_grads, void* const* in_grads, size_t budget,
                       cudaStream_t s);
+void prepare_adjoint_impl(GraphImpl& g, AdjointState& st, size_t budget);
 std::shared_ptr<AdjointState> new_adjoint_state();
 size_t adjoint_tape_bytes(const AdjointState& st);
 bool adjoint_chunked(const AdjointState& st);
@@ -239,9 +254,10 @@ CodegenOut gen_map_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
 CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
 CodegenOut gen_batch_kernel(const GraphImpl& g, const Group& grp, int s0, int s1);
 CodegenOut gen_axis_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
-// adjoint kernels
-CodegenOut gen_map_adjoint_kernel(const GraphImpl& g, const Group& grp, bool vec_ok);
-CodegenOut gen_stencil_adjoint_kernel(const GraphImpl& g, const Group& grp, int step);
+// reverse of a chunk of a 1-D / 2-D stencil chain, forward recomputed in the tile
+CodegenOut gen_adj_kernel(const GraphImpl& g, const Group& grp);
+// does the reverse of epilogue chain `epi` read a value other than its output?
+bool adj_needs_z(const std::vector<std::pair<int, double>>& epi);
 
 // Steps per chunk of a deferred common-weight run of stencil node n's steps
 // (0: plain weighted sum; INT32_MAX: no growth bound).

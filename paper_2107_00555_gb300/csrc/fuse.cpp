@@ -59,6 +59,7 @@ struct Planner {
     const Group& G = g.groups[gi];
     if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce) return in_vec(G.members, v);
     if (G.kind == GroupKind::Stencil) return v == G.st_out || in_vec(G.post, v);
+    if (G.kind == GroupKind::AdjTile) return v == G.st_out;
     return false;
   }
 
@@ -105,6 +106,7 @@ struct Planner {
         case Kind::Map: plan_map(v); break;
         case Kind::Reduce: plan_reduce(v); break;
         case Kind::Stencil: plan_stencil(v); break;
+        case Kind::AdjChain: plan_adj(v); break;
       }
     }
     if (flags & DCP_BATCH) plan_batch();
@@ -139,7 +141,9 @@ struct Planner {
         if (G.shape != n.shape) continue;
         if (G.kind == GroupKind::Map && !fmaps()) continue;
         if (G.kind == GroupKind::Stencil && !fsub()) continue;
-        if (G.kind == GroupKind::Batch || G.kind == GroupKind::AxisReduce) continue;
+        if (G.kind == GroupKind::Batch || G.kind == GroupKind::AxisReduce ||
+            G.kind == GroupKind::AdjTile)
+          continue;
         bool ok = true;
         for (int b : n.in)
           if (!computed_in(gi, b) && !available_before(b, gi)) ok = false;
@@ -255,7 +259,8 @@ struct Planner {
     int a = n.in[0];
     int gi = g.value_group[a];
     if (fsub() && gi >= 0 && computed_in(gi, a) && g.groups[gi].kind != GroupKind::Batch &&
-        g.groups[gi].kind != GroupKind::AxisReduce && (int)g.groups[gi].reds.size() < kMaxIO) {
+        g.groups[gi].kind != GroupKind::AxisReduce && g.groups[gi].kind != GroupKind::AdjTile &&
+        (int)g.groups[gi].reds.size() < kMaxIO) {
       g.groups[gi].reds.push_back(v);
       g.value_group[v] = gi;
       return;
@@ -348,6 +353,31 @@ struct Planner {
     for (int m : S.members) g.value_group[m] = si;
   }
 
+  // Reverse of a chunk of a stencil chain (built by the adjoint): one group
+  // reading u_t and the cotangent of u_{t+k} from memory, storing the
+  // cotangent of u_t.
+  void plan_adj(int v) {
+    const Node& n = g.nodes[v];
+    Group A;
+    A.kind = GroupKind::AdjTile;
+    A.dtype = n.dtype;
+    A.shape = n.shape;
+    A.bc = n.bc;
+    A.offsets = pad_offsets(n);
+    for (int d = 0; d < 3; ++d) {
+      int r = 0;
+      for (int k = 0; k < n.npts(); ++k) r = std::max(r, std::abs(A.offsets[k * 3 + d]));
+      A.radius[d] = r;
+    }
+    A.loads = {n.in[0], n.in[1]};
+    A.st_in = n.in[0];
+    A.st_out = v;
+    A.depth = (int)n.chain.size();
+    A.members.push_back(v);
+    g.groups.push_back(A);
+    g.value_group[v] = (int)g.groups.size() - 1;
+  }
+
   // Pack independent stencil groups that run one step program into batches.
   void plan_batch() {
     std::map<std::string, std::vector<int>> classes;
@@ -432,6 +462,7 @@ struct Planner {
         cand.push_back(G.st_out);
         cand.insert(cand.end(), G.post.begin(), G.post.end());
       }
+      if (G.kind == GroupKind::AdjTile) cand.push_back(G.st_out);
       for (int v : cand) {
         bool need = is_out[v];
         for (int u : users[v])
@@ -459,6 +490,15 @@ struct Planner {
         G.unroll = (int)opt(DCP_OPT_MAP_UNROLL, 2);
         nl += 1;
       } else if (G.kind == GroupKind::AxisReduce) {
+        G.threads = 256;
+        nl += 1;
+      } else if (G.kind == GroupKind::AdjTile) {
+        // output tile; the halo is 2 k r (the forward k steps grow the
+        // region the reverse k steps consume)
+        const bool one_d = G.shape.size() == 1;
+        G.tile[0] = 1;
+        G.tile[1] = one_d ? 1 : (int)opt(DCP_OPT_TILE_Y, G.dtype == DCP_F32 ? 32 : 16);
+        G.tile[2] = (int)opt(DCP_OPT_TILE_X, one_d ? 512 : 32);
         G.threads = 256;
         nl += 1;
       } else {

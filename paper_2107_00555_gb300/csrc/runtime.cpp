@@ -180,6 +180,18 @@ static std::vector<LaunchSpec> build_group_launches(GraphImpl& g, int gi) {
     L.push_back(std::move(ls));
     return L;
   }
+  if (G.kind == GroupKind::AdjTile) {
+    LaunchSpec ls;
+    ls.group = gi;
+    ls.s1 = G.depth;
+    ls.code = gen_adj_kernel(g, G);
+    if (ls.code.smem_bytes > 227 * 1024)
+      fail(DCP_E_UNSUPPORTED, "reverse stencil tile needs " + std::to_string(ls.code.smem_bytes) +
+                                  " bytes of shared memory; lower the tile or the reverse depth");
+    nvrtc_compile(ls.code.source, ls.code.name, &ls.compile_ms, nullptr);
+    L.push_back(std::move(ls));
+    return L;
+  }
   if (G.kind == GroupKind::Map) {
     LaunchSpec ls;
     ls.group = gi;
@@ -651,6 +663,29 @@ static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const v
            "cuLaunchKernel(batch)");
 }
 
+// Time-tiled reverse of a stencil chain chunk: one CTA per output tile.
+static void launch_adj(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
+                       cudaStream_t s) {
+  const Group& G = g.groups[ls.group];
+  StParamsH p;
+  std::memset(&p, 0, sizeof p);
+  dims3(G.shape, p.nz, p.ny, p.nx);
+  if ((int64_t)p.nz * p.ny * p.nx == 0) return;
+  p.ld[0] = ptr[G.loads[0]];
+  p.ld[1] = ptr[G.loads[1]];
+  p.st[0] = const_cast<void*>(ptr[G.st_out]);
+  const int TX = G.tile[2], TY = G.shape.size() == 1 ? 1 : G.tile[1];
+  p.tiles_x = (p.nx + TX - 1) / TX;
+  p.tiles_y = (p.ny + TY - 1) / TY;
+  p.tiles_z = 1;
+  const int64_t gx = (int64_t)p.tiles_x * p.tiles_y;
+  if (gx > 0x7fffffff) fail(DCP_E_SHAPE, "grid too large");
+  void* args[] = {&p};
+  check_cu(drv().launchKernel(ls.fn, (unsigned)gx, 1, 1, ls.code.threads, 1, 1,
+                              ls.code.smem_bytes, (CUstream)s, args, nullptr),
+           "cuLaunchKernel(reverse stencil)");
+}
+
 static void launch_one(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
                        cudaStream_t s) {
   maybe_inject("launch", DCP_E_CUDA);
@@ -658,6 +693,7 @@ static void launch_one(GraphImpl& g, LaunchSpec& ls, const std::vector<const voi
   if (G.kind == GroupKind::Map) launch_map(g, ls, ptr, s);
   else if (G.kind == GroupKind::AxisReduce) launch_axis(g, ls, ptr, s);
   else if (G.kind == GroupKind::Stencil) launch_stencil(g, ls, ptr, s);
+  else if (G.kind == GroupKind::AdjTile) launch_adj(g, ls, ptr, s);
   else launch_batch(g, ls, ptr, s);
 }
 
@@ -882,7 +918,8 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
   check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
   for (int gi = 0; gi < (int)g.groups.size(); ++gi) {
     const Group& G = g.groups[gi];
-    if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce) {
+    if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce ||
+        G.kind == GroupKind::AdjTile) {
       launch_group(g, gi, ptr, s);
       continue;
     }
@@ -1096,7 +1133,10 @@ std::string describe_plan(const GraphImpl& g) {
                            ? "map"
                            : (G.kind == GroupKind::Stencil
                                   ? "stencil"
-                                  : (G.kind == GroupKind::AxisReduce ? "axis_reduce" : "batch"));
+                                  : (G.kind == GroupKind::AxisReduce
+                                         ? "axis_reduce"
+                                         : (G.kind == GroupKind::AdjTile ? "reverse_tile"
+                                                                         : "batch")));
     os << "{\"kind\": \"" << kind << "\", \"dtype\": \"" << dtype_name(G.dtype) << "\", \"shape\": [";
     for (size_t i = 0; i < G.shape.size(); ++i) os << (i ? ", " : "") << G.shape[i];
     os << "], \"members\": " << G.members.size() << ", \"post\": " << G.post.size()
@@ -1107,12 +1147,14 @@ std::string describe_plan(const GraphImpl& g) {
     if (G.kind == GroupKind::Batch) os << ", \"instances\": " << G.batch_members.size();
     if (G.kind == GroupKind::AxisReduce) os << ", \"axis\": " << G.axis;
     if (G.kind == GroupKind::Stencil && G.shape.size() == 3) os << ", \"cells_per_thread\": " << G.cx;
-    if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce)
+    if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce && G.kind != GroupKind::AdjTile)
       os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
          << ", \"prefetch\": " << G.prefetch << ", \"threads\": " << G.threads
          << ", \"min_ctas\": " << G.min_ctas;
     int epi = 0;
     for (const StepDesc& s : G.steps) epi += (int)s.epi.size();
+    if (G.kind == GroupKind::AdjTile)
+      for (const AdjStep& s : g.nodes[G.st_out].chain) epi += (int)s.epi.size();
     os << ", \"epilogue_ops\": " << epi << "}";
   }
   os << "], \"launches\": [";
@@ -1164,6 +1206,11 @@ void run_adjoint(GraphImpl& g, const void* const* inputs, const void* const* out
   ensure_device(g);
   if (!g.adj) g.adj = new_adjoint_state();
   run_adjoint_impl(g, *g.adj, inputs, out_grads, in_grads, budget, s);
+}
+
+void prepare_adjoint(GraphImpl& g, size_t budget) {
+  if (!g.adj) g.adj = new_adjoint_state();
+  prepare_adjoint_impl(g, *g.adj, budget);
 }
 
 }  // namespace dcp

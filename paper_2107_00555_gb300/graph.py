@@ -239,6 +239,11 @@ class Graph:
                           tape_budget_bytes, stream.cuda_stream)
         return in_grads
 
+    def prepare_adjoint(self, tape_budget_bytes=1 << 62):
+        """Plan and compile the reverse pass without running it (no GPU needed)."""
+        C.dcp_prepare_adjoint(self._h, tape_budget_bytes)
+        return self.plan()
+
     def sync(self, stream=None):
         import torch
         s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream

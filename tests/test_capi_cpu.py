@@ -424,3 +424,73 @@ def test_deferred_weight_option_and_run_start():
     g.fuse(C.DCP_FUSE_ALL)
     assert scales(g)[0] is None and scales(g)[1:4] == [1.0] * 3
     assert scales(g)[4] == pytest.approx(1e-4, rel=1e-15)
+
+
+def _chain2d(shape, steps, bc, dtype, epi=("tanh",), depth=None, radius2=False):
+    offs = programs.FIVE_POINT if not radius2 else [(0, 0), (0, -2), (0, 2), (2, 0), (-2, 0)]
+    g = Graph()
+    u = g.input(dtype, shape)
+    for _ in range(steps):
+        u = g.stencil(u, offs, programs.FIVE_WEIGHTS, bc, 1)
+        for e in epi:
+            u = g.map(e, [u])
+    g.output(g.reduce(g.map("square", [u]), "sum"))
+    if depth is not None:
+        g.set_option(C.DCP_OPT_ADJOINT_DEPTH, depth)
+    g.fuse(C.DCP_FUSE_ALL)
+    return g
+
+
+def _adj_kernels(plan, prefix):
+    return [l for l in plan["adjoint"]["launches"] if l["kernel"].startswith(prefix)]
+
+
+def test_plan_time_tiled_reverse():
+    """dcp_prepare_adjoint plans and compiles the reverse pass without a GPU.
+    A float32 2-D tanh chain of 10 steps with DCP_OPT_ADJOINT_DEPTH = 4 runs
+    its reverse in chunks of 4: the forward pass stores only u_4 and u_8 and
+    stops there (the last chunk's states are recomputed in its tile), the
+    reverse is one broadcast of the loss cotangent and 3 chunk launches
+    (2 + 4 + 4 steps).  The default (0) is one launch per step and the full
+    tape."""
+    state = 64 * 80 * 4
+    p = _chain2d((64, 80), 10, "periodic", "f32", depth=4).prepare_adjoint()
+    a = p["adjoint"]
+    assert a["tape_bytes"] == 2 * state and not a["checkpointed"]
+    assert len(_adj_kernels(p, "dcp_adj_")) == 3
+    assert [l["phase"] for l in a["launches"]] == ["forward"] * 2 + ["reverse"] * 4
+    assert len(set(l["kernel"] for l in _adj_kernels(p, "dcp_adj_"))) == 2  # 2-step and 4-step
+    p0 = _chain2d((64, 80), 10, "periodic", "f32").prepare_adjoint()
+    assert p0["adjoint"]["tape_bytes"] == 10 * state
+    assert not _adj_kernels(p0, "dcp_adj_") and len(p0["adjoint"]["launches"]) == 20
+
+
+def test_plan_time_tiled_reverse_rules():
+    """3-D chains and chains linear up to their last step never take the
+    tiled form; every 1-D / 2-D form compiles for both boundaries, radius 2
+    and epilogues whose reverse needs the pre-epilogue value."""
+    p = _chain2d((30, 40), 6, "zero", "f64", depth=3).prepare_adjoint()
+    assert len(_adj_kernels(p, "dcp_adj_")) == 2
+    lin = _chain2d((30, 40), 6, "zero", "f32", epi=(), depth=3).prepare_adjoint()
+    assert not _adj_kernels(lin, "dcp_adj_")
+    g3 = programs.tanh_chain((8, 9, 10), 4, "periodic", "f32")
+    g3.set_option(C.DCP_OPT_ADJOINT_DEPTH, 2)
+    g3.fuse(C.DCP_FUSE_ALL)
+    assert not _adj_kernels(g3.prepare_adjoint(), "dcp_adj_")
+    for dt, bc, epi in (("f32", "zero", ("tanh",)), ("f32", "periodic", ("sin", "square")),
+                        ("f64", "zero", ("exp", "sqrt")), ("f64", "periodic", ("abs", "cos"))):
+        for shape in ((50,), (20, 30)):
+            p = _chain2d(shape, 5, bc, dt, epi, depth=2,
+                         radius2=len(shape) == 2 and epi[0] == "sin").prepare_adjoint()
+            assert len(_adj_kernels(p, "dcp_adj_")) == 3
+    g = _chain2d((20, 30), 4, "zero", "f32")
+    with pytest.raises(DcpError) as e:
+        g.set_option(C.DCP_OPT_ADJOINT_DEPTH, 1)  # after dcp_fuse
+    assert e.value.status == C.DCP_E_STATE
+    g = Graph()
+    with pytest.raises(DcpError) as e:
+        g.set_option(C.DCP_OPT_ADJOINT_DEPTH, 65)
+    assert e.value.status == C.DCP_E_INVALID_ARG
+    with pytest.raises(DcpError) as e:
+        C.dcp_prepare_adjoint(g._h, 1 << 20)  # before dcp_fuse
+    assert e.value.status == C.DCP_E_STATE

@@ -522,6 +522,18 @@ class Stencil(Workload):
         self.g0 = build(self.shape, self.T, self.bc, self.dtype, fuse=0)
         self.out = self.g.empty_outputs(dev)
         self.out0 = self.g0.empty_outputs(dev)
+        self.call_coop = None
+        if self.name == "jacobi2d":
+            # the cooperative form: all 10 steps in one launch on 152 tiles of
+            # 14 x 32, neighbour flags between steps (graph replay as well)
+            self.gc = build(self.shape, self.T, self.bc, self.dtype)
+            self.gc.set_option(C.DCP_OPT_STENCIL_KERNEL, 2)
+            self.gc.set_option(C.DCP_OPT_TILE_Y, 14)
+            self.gc.set_option(C.DCP_OPT_TILE_X, 32)
+            self.gc.set_option(C.DCP_OPT_USE_GRAPH, 1)
+            self.gc.fuse(C.DCP_FUSE_ALL)
+            self.outc = self.gc.empty_outputs(dev)
+            self.call_coop = self.gc.prepare(self.dev, self.outc)
         # buffers marshalled once: a step is one C call (the 256^2 run is
         # shorter than the Python-side checks of an unprepared call)
         self.call = self.g.prepare(self.dev, self.out)
@@ -539,7 +551,10 @@ class Stencil(Workload):
         self.call0()
 
     def legs(self):
-        return [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
+        legs = [("op_by_op", self.step_opbyop, self.n_launch0), ("torch_eager", self.step_torch, None)]
+        if self.call_coop is not None:
+            legs.append(("cooperative_one_launch", self.call_coop, 1))
+        return legs
 
     def step_torch(self):
         """The paper's NumPy form as torch eager ops (slices into temporaries)."""

@@ -113,7 +113,9 @@ enum {
   DCP_OPT_TILE_Y = 3,          /* stencil tile extent along y */
   DCP_OPT_MAP_BLOCKS_PER_SM = 4, /* CTAs per SM for map/reduce kernels */
   DCP_OPT_USE_GRAPH = 5,       /* 1: replay a captured CUDA graph in dcp_run */
-  DCP_OPT_STENCIL_KERNEL = 7,  /* 2-D stencils: 0 shared-memory tiles, 1 warp stream */
+  DCP_OPT_STENCIL_KERNEL = 7,  /* 1-D / 2-D stencils: 0 shared-memory tiles, 1 warp stream,
+                                  2 cooperative: every step in one launch, one tile per
+                                  resident CTA, neighbour flags between steps (small grids) */
   DCP_OPT_HOST_ACCESS = 8,     /* dcp_run_host: 1 (default) kernels access page-locked host
                                   buffers directly, 0 always stage through device copies */
   DCP_OPT_STREAM_ROWS = 9,     /* warp-stream stencils: rows per work item (>= 1) */

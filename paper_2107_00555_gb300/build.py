@@ -33,7 +33,8 @@ EMBED = [("dcp_device.cuh", "device_header_source"),
          ("k_stencil2d_stream.cuh", "kernel_stream_source"),
          ("k_axis.cuh", "kernel_axis_source"),
          ("k_math64.cuh", "kernel_math64_source"),
-         ("k_stencil_adj.cuh", "kernel_adj_source")]
+         ("k_stencil_adj.cuh", "kernel_adj_source"),
+         ("k_stencil2d_coop.cuh", "kernel_coop_source")]
 
 
 def _embed_source() -> str:

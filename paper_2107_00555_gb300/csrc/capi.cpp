@@ -409,6 +409,7 @@ dcp_status dcp_set_option(dcp_graph gh, int32_t key, int64_t v) {
     if (key == DCP_OPT_TILE_X && (v < 8 || v > 512 || v % 8)) fail(DCP_E_INVALID_ARG, "tile x must be a multiple of 8 in 8..512");
     if (key == DCP_OPT_TILE_Y && (v < 1 || v > 512)) fail(DCP_E_INVALID_ARG, "tile y must be in 1..512");
     if (key == DCP_OPT_MAP_BLOCKS_PER_SM && (v < 1 || v > 32)) fail(DCP_E_INVALID_ARG, "blocks per SM must be 1..32");
+    if (key == DCP_OPT_STENCIL_KERNEL && v > 2) fail(DCP_E_INVALID_ARG, "stencil kernel form must be 0, 1 or 2");
     if (key == DCP_OPT_STREAM_ROWS && (v < 1 || v > (1 << 30))) fail(DCP_E_INVALID_ARG, "rows per work item must be >= 1");
     if (key == DCP_OPT_TILE_Z && (v < 1 || v > 1024)) fail(DCP_E_INVALID_ARG, "tile z must be in 1..1024");
     if (key == DCP_OPT_STREAM_PREFETCH && (v < 1 || v > 4)) fail(DCP_E_INVALID_ARG, "stream prefetch must be in 1..4");

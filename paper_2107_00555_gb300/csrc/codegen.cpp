@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <sstream>
@@ -146,7 +147,8 @@ uint64_t skeleton_hash(const std::string& body) {
       {"k_stencil2d_stream.cuh", kernel_stream_source()},
       {"k_axis.cuh", kernel_axis_source()},
       {"k_math64.cuh", kernel_math64_source()},
-      {"k_stencil_adj.cuh", kernel_adj_source()}};
+      {"k_stencil_adj.cuh", kernel_adj_source()},
+      {"k_stencil2d_coop.cuh", kernel_coop_source()}};
   for (const auto& k : skel)
     if (body.find(std::string("#include \"") + k.first + "\"") != std::string::npos) text += k.second;
   return fnv1a(text);
@@ -618,10 +620,15 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
   CodegenOut out;
   out.threads = threads;
   out.guard_max_input = guard.on ? guard.max_input : 0.0;
+  // cooperative form: every step in one launch, a halo of one radius
+  const bool coop = G.variant == 2 && nd <= 2 && !batch;
+  if (coop && (!first || !last))
+    fail(DCP_E_UNSUPPORTED, "the cooperative stencil form runs every step in one launch");
   if (nd <= 2) {
     const int TX = G.tile[2], TY = nd == 1 ? 1 : G.tile[1];
     const int RY = nd == 1 ? 0 : ry;
-    const int PW = TX + 2 * nsteps * rx, PH = TY + 2 * nsteps * RY;
+    const int hs = coop ? 1 : nsteps;  // halo width in radii
+    const int PW = TX + 2 * hs * rx, PH = TY + 2 * hs * RY;
     os << "#define DCP_TX " << TX << "\n#define DCP_TY " << TY << "\n#define DCP_RX " << rx
        << "\n#define DCP_RY " << RY << "\n#define DCP_NSTEPS " << nsteps << "\n";
     if (!batch) emit_stencil_io(os, g, G, first, last);
@@ -655,7 +662,15 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     os << "template <int S> __device__ __forceinline__ DCP_T dcp_sum(const DCP_T* A, int c, "
           "const DCP_T (&km)[DCP_NK]);\n";
     os << sums.str();
-    os << "#include \"k_stencil2d.cuh\"\n";
+    if (coop) {
+      // host-side fault injection (DCP_FAULT=coop_wait): every neighbour wait
+      // gives up after 1000 polls, so the bounded-wait error path runs
+      // without a fault or a hang
+      const char* f = std::getenv("DCP_FAULT");
+      if (f && std::strcmp(f, "coop_wait") == 0)
+        os << "#define DCP_SPIN_LIMIT 1000\n#define DCP_WAIT_SKEW 4096u\n";
+    }
+    os << (coop ? "#include \"k_stencil2d_coop.cuh\"\n" : "#include \"k_stencil2d.cuh\"\n");
     out.smem_bytes = 2 * PW * PH * dtype_size(T);
     for (double x : scales)
       if (x != 0.0) out.defer_scales = scales;
@@ -727,7 +742,8 @@ CodegenOut gen_stencil_kernel(const GraphImpl& g, const Group& G, int s0, int s1
     os << "#include \"k_stencil3d.cuh\"\n";
     out.smem_bytes = (2 * rz + 2) * PW * PH * dtype_size(T);
   }
-  out.source = finish(batch ? "dcp_batch" : (nd == 3 ? "dcp_st3d" : "dcp_st2d"), os.str());
+  out.source = finish(batch ? "dcp_batch" : (nd == 3 ? "dcp_st3d" : (coop ? "dcp_coop" : "dcp_st2d")),
+                      os.str());
   out.name = kname_of(out.source);
   return out;
 }

@@ -38,6 +38,8 @@ struct Driver {
   CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
   CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
                            unsigned, CUstream, void**, void**) = nullptr;
+  CUresult (*launchCooperative)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
+                                unsigned, unsigned, CUstream, void**) = nullptr;
   CUresult (*getErrorString)(CUresult, const char**) = nullptr;
 };
 const Driver& drv();
@@ -140,7 +142,8 @@ struct Group {
   int tile[3] = {1, 1, 1};      // output tile (z, y, x) for stencils
   int threads = 256;
   int blocks_per_sm = 4;
-  int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream
+  int variant = 0;              // stencils: 0 = shared-memory tile, 1 = warp stream,
+                                //           2 = cooperative (every step in one launch)
   int seg = 0;                  // warp stream: rows per work item (single arrays)
   int prefetch = 1;             // warp stream: rows requested ahead, in row windows (2*ry+1)
   int min_ctas = 0;             // warp stream: CTAs per SM the register budget must allow (0: any)
@@ -185,6 +188,7 @@ const char* kernel_stream_source();     // k_stencil2d_stream.cuh
 const char* kernel_axis_source();       // k_axis.cuh
 const char* kernel_math64_source();     // k_math64.cuh
 const char* kernel_adj_source();        // k_stencil_adj.cuh
+const char* kernel_coop_source();       // k_stencil2d_coop.cuh
 
 // ---------------------------------------------------------------------------
 // Graph object
@@ -273,6 +277,9 @@ inline int stream_width(const Group& G) {
   return 32 * stream_cols_per_lane(G.dtype) - 2 * G.depth * G.radius[2];
 }
 bool stream_eligible(const Group& G, int depth);
+// can the cooperative form run this group with a ty x tx tile (steps <= 63,
+// 1-D / 2-D, each ragged edge tile at least a radius wide)?
+bool coop_eligible(const Group& G, int ty, int tx);
 constexpr int kMaxRadius = 4;
 constexpr int kMaxPoints = 32;
 

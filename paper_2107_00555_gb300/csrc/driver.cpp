@@ -37,6 +37,7 @@ const Driver& drv() {
            get("cuFuncSetAttribute", g_drv.funcSetAttribute) &&
            get("cuOccupancyMaxActiveBlocksPerMultiprocessor", g_drv.occupancy) &&
            get("cuLaunchKernel", g_drv.launchKernel) &&
+           get("cuLaunchCooperativeKernel", g_drv.launchCooperative) &&
            get("cuGetErrorString", g_drv.getErrorString);
   });
   if (!g_ok) fail(DCP_E_CUDA, g_err.empty() ? "CUDA driver unavailable" : g_err);

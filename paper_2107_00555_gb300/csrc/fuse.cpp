@@ -522,6 +522,20 @@ struct Planner {
     int var = stream_eligible(G, G.depth) ? 1 : 0;
     auto it = g.options.find(DCP_OPT_STENCIL_KERNEL);
     if (it != g.options.end()) var = (it->second == 1 && stream_eligible(G, G.depth)) ? 1 : 0;
+    if (it != g.options.end() && it->second == 2 && G.kind == GroupKind::Stencil &&
+        G.shape.size() <= 2) {
+      // cooperative form: every step in one launch on the tile the options
+      // (or the defaults) give
+      G.depth = (int)G.steps.size();
+      if (!coop_eligible(G, G.tile[1], G.tile[2]))
+        fail(DCP_E_UNSUPPORTED, "the cooperative stencil form needs at most 63 steps and edge "
+                                "tiles at least a radius wide");
+      var = 2;
+      // one thread per tile cell (64..1024): the tile's cells are independent
+      // chains, which a latency-bound small grid needs in flight
+      const int cells = (G.shape.size() == 1 ? 1 : G.tile[1]) * G.tile[2];
+      G.threads = std::min(1024, std::max(64, (cells + 31) / 32 * 32));
+    }
     G.variant = var;
     if (var == 1) {
       G.threads = (int)opt(DCP_OPT_STREAM_THREADS, 64);
@@ -575,6 +589,20 @@ struct Planner {
 };
 
 }  // namespace
+
+bool coop_eligible(const Group& G, int ty, int tx) {
+  const int nd = (int)G.shape.size();
+  if (G.kind != GroupKind::Stencil || nd > 2 || G.steps.empty() || G.steps.size() > 63) return false;
+  const int64_t ny = nd == 2 ? G.shape[0] : 1, nx = G.shape.back();
+  if (nd == 1) ty = 1;
+  const int ry = nd == 2 ? G.radius[1] : 0, rx = G.radius[2];
+  if (ty < std::max(1, ry) || tx < std::max(1, rx) || ny < 1 || nx < 1) return false;
+  // the halo must come from the adjacent tiles only
+  const int64_t ey = ny % ty, ex = nx % tx;
+  if ((ey != 0 && ey < ry) || (ex != 0 && ex < rx)) return false;
+  if (ny < ry || nx < rx) return false;
+  return true;
+}
 
 bool stream_eligible(const Group& G, int depth) {
   const int nd = G.kind == GroupKind::Batch ? 2 : (int)G.shape.size();

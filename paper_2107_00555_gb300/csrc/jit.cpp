@@ -70,12 +70,12 @@ CubinRef nvrtc_compile(const std::string& src, const std::string& name, double* 
   auto t0 = std::chrono::steady_clock::now();
   const char* hdr_src[] = {device_header_source(), kernel_map_source(), kernel_stencil2d_source(),
                            kernel_stencil3d_source(), kernel_stream_source(), kernel_axis_source(),
-                           kernel_math64_source(), kernel_adj_source()};
+                           kernel_math64_source(), kernel_adj_source(), kernel_coop_source()};
   const char* hdr_name[] = {"dcp_device.cuh", "k_map.cuh", "k_stencil2d.cuh", "k_stencil3d.cuh",
                             "k_stencil2d_stream.cuh", "k_axis.cuh", "k_math64.cuh",
-                            "k_stencil_adj.cuh"};
+                            "k_stencil_adj.cuh", "k_stencil2d_coop.cuh"};
   nvrtcProgram prog;
-  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 8, hdr_src,
+  nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), (name + ".cu").c_str(), 9, hdr_src,
                                      hdr_name);
   if (r != NVRTC_SUCCESS) fail(DCP_E_COMPILE, std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r));
   // DCP_PTXAS_VERBOSE=1 prints the assembler's register / spill report of

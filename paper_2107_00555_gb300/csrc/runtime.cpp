@@ -46,6 +46,15 @@ struct StParamsH {
   void* ticket;
   void* guard;
 };
+// Cooperative stencil form: the stencil parameters plus the exchange
+// arrays, the per-tile flags, the epoch counter and the error word.
+struct CoopParamsH {
+  StParamsH s;
+  void* xb[2];
+  void* flags;
+  void* ctr;
+  void* err;
+};
 struct AxParamsH {
   const void* ld[kMaxIO];
   const void* sc[kMaxIO];
@@ -72,6 +81,7 @@ struct BatchParamsH {
   void* guard;
 };
 static_assert(sizeof(StParamsH) == 5 * kMaxIO * 8 + 32 + 24, "stencil params layout");
+static_assert(sizeof(CoopParamsH) == sizeof(StParamsH) + 5 * 8, "cooperative params layout");
 static_assert(sizeof(BatchParamsH) == 32, "batch params layout");
 static_assert(sizeof(InstH) == 32, "instance layout");
 
@@ -108,6 +118,10 @@ struct GroupRT {
   // its first launch saw, and the bound that keeps the run finite (0: none)
   unsigned long long* guard = nullptr;
   double guard_bound = 0.0;
+  // cooperative form: per-tile flags, [epoch, CTAs finished], error word
+  unsigned* coop_flags = nullptr;
+  int64_t coop_ntiles = 0;
+  unsigned* coop_ctr = nullptr;
 };
 
 int64_t numel(const std::vector<int64_t>& s) {
@@ -520,6 +534,9 @@ static void* arm_guard(GraphImpl& g, const LaunchSpec& ls, cudaStream_t s) {
   return R.guard;
 }
 
+static void launch_coop(GraphImpl& g, LaunchSpec& ls, const StParamsH& sp, int64_t tiles,
+                        cudaStream_t s);
+
 static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
                            cudaStream_t s) {
   auto& rt = *g.rt;
@@ -572,10 +589,51 @@ static void launch_stencil(GraphImpl& g, LaunchSpec& ls, const std::vector<const
     p.ticket = rt.grt[ls.group].ticket;
   }
   p.guard = arm_guard(g, ls, s);
+  if (G.variant == 2) {
+    launch_coop(g, ls, p, gx, s);
+    return;
+  }
   void* args[] = {&p};
   check_cu(drv().launchKernel(ls.fn, (unsigned)gx, (unsigned)p.tiles_z, 1, ls.code.threads, 1, 1,
                               ls.code.smem_bytes, (CUstream)s, args, nullptr),
            "cuLaunchKernel(stencil)");
+}
+
+// Cooperative form: one launch runs every step; neighbouring tiles
+// exchange their border rings through the group's two state arrays.
+static void launch_coop(GraphImpl& g, LaunchSpec& ls, const StParamsH& sp, int64_t tiles,
+                        cudaStream_t s) {
+  auto& rt = *g.rt;
+  GroupRT& R = rt.grt[ls.group];
+  if (tiles > (int64_t)rt.sms * ls.occupancy)
+    fail(DCP_E_UNSUPPORTED, "the cooperative stencil form needs every tile resident: " +
+                                std::to_string(tiles) + " tiles, " +
+                                std::to_string((int64_t)rt.sms * ls.occupancy) + " resident CTAs");
+  if (!R.coop_ctr) {
+    R.coop_ctr = (unsigned*)dalloc(rt, 256);  // [0] epoch, [1] finished CTAs, [2] error word
+    check_cuda(cudaMemset(R.coop_ctr, 0, 256), "cudaMemset(coop counters)");
+  }
+  if (R.coop_ntiles < tiles) {
+    // a new flag table starts from epoch 0 with every flag 0 (behind every
+    // target), both reset in stream order after the launches before it
+    R.coop_flags = (unsigned*)dalloc(rt, (size_t)tiles * sizeof(unsigned));
+    check_cuda(cudaMemsetAsync(R.coop_flags, 0, (size_t)tiles * sizeof(unsigned), s),
+               "cudaMemsetAsync(flags)");
+    check_cuda(cudaMemsetAsync(R.coop_ctr, 0, 2 * sizeof(unsigned), s), "cudaMemsetAsync(epoch)");
+    R.coop_ntiles = tiles;
+  }
+  CoopParamsH p;
+  std::memset(&p, 0, sizeof p);
+  p.s = sp;
+  p.xb[0] = group_state(g, ls.group, 0);
+  p.xb[1] = group_state(g, ls.group, 1);
+  p.flags = R.coop_flags;
+  p.ctr = R.coop_ctr;
+  p.err = R.coop_ctr + 2;
+  void* args[] = {&p};
+  check_cu(drv().launchCooperative(ls.fn, (unsigned)tiles, 1, 1, ls.code.threads, 1, 1,
+                                   ls.code.smem_bytes, (CUstream)s, args),
+           "cuLaunchCooperativeKernel(stencil)");
 }
 
 static void launch_batch(GraphImpl& g, LaunchSpec& ls, const std::vector<const void*>& ptr,
@@ -842,6 +900,9 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
       if (i >= base_tiles)
         for (int th : {512, 1024}) c.push_back({d, 1, t[0], t[1], th});
     }
+  // (the cooperative form, tz slot = -2, is not a candidate: on the 256^2
+  // f64 average its neighbour exchanges through L2 cost about 3.8 us per
+  // step, twice the time per step of two time-tiled launches)
   // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item,
   // 0 = planner's; tx slot = row windows requested ahead)
   for (int d : {1, 2, 3, 4, 5, 6, 8, 10})
@@ -866,7 +927,7 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
 void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
   Group& G = g.groups[gi];
   G.depth = cfg[0];
-  G.variant = cfg[1] < 0 ? 1 : 0;
+  G.variant = cfg[1] == -1 ? 1 : (cfg[1] == -2 ? 2 : 0);
   G.tile[0] = cfg[1] < 0 ? 1 : cfg[1];
   G.tile[1] = cfg[2];
   G.tile[2] = cfg[3];
@@ -891,6 +952,14 @@ void apply_config(GraphImpl& g, int gi, const TuneCfg& cfg) {
   }
   std::vector<LaunchSpec> L = build_group_launches(g, gi);
   for (auto& ls : L) load_launch(ls);
+  if (G.variant == 2) {
+    // every tile must be resident at once
+    const int nd = group_nd(G);
+    const int64_t ny = nd == 2 ? G.shape[0] : 1, nx = G.shape.back();
+    const int64_t tiles = ((ny + G.tile[1] - 1) / G.tile[1]) * ((nx + G.tile[2] - 1) / G.tile[2]);
+    if (tiles > (int64_t)g.rt->sms * L[0].occupancy)
+      fail(DCP_E_UNSUPPORTED, "cooperative candidate does not fit the resident CTAs");
+  }
   auto& all = g.rt->launches;
   std::vector<LaunchSpec> merged;
   bool placed = false;
@@ -918,8 +987,9 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
   check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
   for (int gi = 0; gi < (int)g.groups.size(); ++gi) {
     const Group& G = g.groups[gi];
+    // (a cooperative group runs as the option asked: it is not a candidate form)
     if (G.kind == GroupKind::Map || G.kind == GroupKind::AxisReduce ||
-        G.kind == GroupKind::AdjTile) {
+        G.kind == GroupKind::AdjTile || G.variant == 2) {
       launch_group(g, gi, ptr, s);
       continue;
     }
@@ -930,8 +1000,9 @@ static void autotune(GraphImpl& g, const std::vector<const void*>& ptr, cudaStre
       launch_group(g, gi, ptr, s);
       continue;
     }
-    TuneCfg best = {G.depth, G.variant == 1 ? -1 : G.tile[0], G.variant == 1 ? G.seg : G.tile[1],
-                    G.variant == 1 ? G.prefetch : G.tile[2], G.cx};
+    TuneCfg best = {G.depth, G.variant == 1 ? -1 : (G.variant == 2 ? -2 : G.tile[0]),
+                    G.variant == 1 ? G.seg : G.tile[1], G.variant == 1 ? G.prefetch : G.tile[2],
+                    G.variant == 2 ? G.threads : G.cx};
     float best_ms = 1e30f;
     for (const auto& cfg : tune_candidates(G, rt.sms)) {
       try {
@@ -1028,6 +1099,16 @@ static void check_guards(GraphImpl& g) {
   auto& rt = *g.rt;
   for (size_t gi = 0; gi < rt.grt.size(); ++gi) {
     GroupRT& R = rt.grt[gi];
+    if (R.coop_ctr) {
+      unsigned err = 0;
+      check_cuda(cudaMemcpy(&err, R.coop_ctr + 2, sizeof err, cudaMemcpyDeviceToHost),
+                 "cudaMemcpy(coop error word)");
+      if (err) {
+        check_cuda(cudaMemset(R.coop_ctr + 2, 0, sizeof err), "cudaMemset(coop error word)");
+        fail(DCP_E_TIMEOUT, "a cooperative stencil launch gave up waiting for a neighbouring tile; "
+                            "its results are not valid");
+      }
+    }
     if (!R.guard || !(R.guard_bound > 0.0)) continue;
     unsigned long long bits = 0;
     check_cuda(cudaMemcpy(&bits, R.guard, sizeof bits, cudaMemcpyDeviceToHost), "cudaMemcpy(guard)");
@@ -1148,7 +1229,7 @@ std::string describe_plan(const GraphImpl& g) {
     if (G.kind == GroupKind::AxisReduce) os << ", \"axis\": " << G.axis;
     if (G.kind == GroupKind::Stencil && G.shape.size() == 3) os << ", \"cells_per_thread\": " << G.cx;
     if (G.kind != GroupKind::Map && G.kind != GroupKind::AxisReduce && G.kind != GroupKind::AdjTile)
-      os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : "tile") << "\", \"seg\": " << G.seg
+      os << ", \"kernel_form\": \"" << (G.variant == 1 ? "stream" : (G.variant == 2 ? "coop" : "tile")) << "\", \"seg\": " << G.seg
          << ", \"prefetch\": " << G.prefetch << ", \"threads\": " << G.threads
          << ", \"min_ctas\": " << G.min_ctas;
     int epi = 0;

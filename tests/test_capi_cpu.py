@@ -494,3 +494,35 @@ def test_plan_time_tiled_reverse_rules():
     with pytest.raises(DcpError) as e:
         C.dcp_prepare_adjoint(g._h, 1 << 20)  # before dcp_fuse
     assert e.value.status == C.DCP_E_STATE
+
+
+def test_plan_cooperative_form():
+    """DCP_OPT_STENCIL_KERNEL = 2 plans every step of a 1-D / 2-D group as one
+    cooperative launch (one thread per tile cell) and compiles it for every
+    boundary; groups it cannot run are rejected on the host."""
+    for bc in ("zero", "periodic", "fixed_ring"):
+        for shape, tile in (((256, 256), (14, 32)), ((1000,), (1, 32))):
+            g = programs.jacobi2d(shape, 10, bc, "f64") if len(shape) == 2 else Graph()
+            if len(shape) == 1:
+                v = g.input("f32", shape)
+                g.output(g.reduce(g.stencil(g.map("tanh", [v]), [(-1,), (0,), (1,)],
+                                            [0.25, 0.5, 0.25], bc, 7), "sum"))
+            g.set_option(C.DCP_OPT_STENCIL_KERNEL, 2)
+            g.set_option(C.DCP_OPT_TILE_Y, tile[0])
+            g.set_option(C.DCP_OPT_TILE_X, tile[1])
+            g.fuse(C.DCP_FUSE_ALL)
+            p = g.plan()
+            (grp,) = [x for x in p["groups"] if x["kind"] == "stencil"]
+            assert grp["kernel_form"] == "coop" and grp["depth"] == grp["steps"]
+            assert grp["threads"] == (448 if len(shape) == 2 else 64)
+            assert len(p["launches"]) == 1 and p["launches"][0]["kernel"].startswith("dcp_coop_")
+    g = programs.jacobi2d((64, 64), 64, "zero", "f64")  # more than 63 steps
+    g.set_option(C.DCP_OPT_STENCIL_KERNEL, 2)
+    assert _err(g.fuse, C.DCP_FUSE_ALL) == C.DCP_E_UNSUPPORTED
+    g2 = Graph()  # an edge tile 1 row tall under a radius of 2
+    v = g2.input("f64", (65, 64))
+    g2.output(g2.stencil(v, [(0, 0), (2, 0), (-2, 0)], [0.5, 0.25, 0.25], "zero", 3))
+    g2.set_option(C.DCP_OPT_STENCIL_KERNEL, 2)
+    g2.set_option(C.DCP_OPT_TILE_Y, 16)
+    assert _err(g2.fuse, C.DCP_FUSE_ALL) == C.DCP_E_UNSUPPORTED
+    assert _err(Graph().set_option, C.DCP_OPT_STENCIL_KERNEL, 3) == C.DCP_E_INVALID_ARG

@@ -901,8 +901,8 @@ std::vector<TuneCfg> tune_candidates(const Group& G, int sms) {
         for (int th : {512, 1024}) c.push_back({d, 1, t[0], t[1], th});
     }
   // (the cooperative form, tz slot = -2, is not a candidate: on the 256^2
-  // f64 average its neighbour exchanges through L2 cost about 3.8 us per
-  // step, twice the time per step of two time-tiled launches)
+  // f64 average its neighbour exchanges through L2 cost about 3.5 us per
+  // step, nearly twice the time per step of two time-tiled launches)
   // warp-stream variant (tz slot = -1 marks it; ty slot = rows per work item,
   // 0 = planner's; tx slot = row windows requested ahead)
   for (int d : {1, 2, 3, 4, 5, 6, 8, 10})

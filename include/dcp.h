@@ -62,7 +62,8 @@ enum {
   DCP_E_OOM = -5,         /* device or host allocation failed (or budget exceeded) */
   DCP_E_CUDA = -6,        /* a CUDA runtime/driver call failed (message has detail) */
   DCP_E_COMPILE = -7,     /* run-time compilation of a fused kernel failed */
-  DCP_E_TIMEOUT = -8,     /* reserved: a bounded device-side wait expired */
+  DCP_E_TIMEOUT = -8,     /* a bounded device-side wait expired (cooperative stencil form;
+                             reported by dcp_sync / dcp_run_host; results invalid) */
   DCP_E_STATE = -9        /* call not allowed in the graph's current state */
 };
 
@@ -249,10 +250,11 @@ dcp_status dcp_run_adjoint(dcp_graph g, const void* const* inputs, const void* c
  * DCP_E_OOM when even sqrt(T) checkpointing exceeds the budget. */
 dcp_status dcp_prepare_adjoint(dcp_graph g, size_t tape_budget_bytes);
 
-/* Waits for `cuda_stream` and reports asynchronous CUDA errors, and
+/* Waits for `cuda_stream` and reports asynchronous CUDA errors,
  * DCP_E_UNSUPPORTED when a deferred common-weight run of the last dcp_run
  * read an input above the magnitude it keeps finite (see dcp_add_stencil;
- * reported once). */
+ * reported once), and DCP_E_TIMEOUT when a cooperative stencil launch gave
+ * up waiting for a neighbouring tile (reported once). */
 dcp_status dcp_sync(dcp_graph g, void* cuda_stream);
 
 /* Overrides a planner choice (DCP_OPT_*).  Allowed before dcp_fuse (tile and

@@ -94,6 +94,27 @@ __device__ __forceinline__ void dcp_cell(const T* __restrict__ A, T* __restrict_
   B[c] = v;
 }
 
+// Border cell i (0 <= i < h w - interior) of an h x w tile whose interior
+// (cells at least a radius from every edge) is ih x iw: the top RY rows, the
+// bottom RY rows, then the RX cells at each side of the rows between.
+__device__ __forceinline__ void dcp_border_cell(int i, int h, int w, int ih, int iw, int& ty,
+                                                int& tx) {
+  const bool has_int = ih > 0 && iw > 0;
+  const int top = has_int ? DCP_RY * w : h * w;
+  if (i < top) {
+    ty = i / w;
+    tx = i - ty * w;
+  } else if (has_int && i < 2 * top) {
+    const int j = i - top;
+    ty = h - DCP_RY + j / w;
+    tx = j % w;
+  } else {
+    const int j = i - 2 * top, r = j / DCP_SIDE, k = j - r * DCP_SIDE;
+    ty = DCP_RY + r;
+    tx = k < DCP_RX ? k : w - 2 * DCP_RX + k;
+  }
+}
+
 template <int S>
 __device__ __forceinline__ void dcp_coop_steps(const DcpCoopParams& q, T*& A, T*& B, int tyi, int txi,
                                                int h, int w, unsigned epoch,
@@ -139,7 +160,7 @@ __device__ __forceinline__ void dcp_coop_steps(const DcpCoopParams& q, T*& A, T*
       const T* __restrict__ X = q.xb[S & 1];
       // halo ring of the shared tile: rows [0, RY) and [RY + h, 2 RY + h),
       // and the side columns of the rows between
-      const int HW = w + 2 * DCP_RX, HH = h + 2 * DCP_RY;
+      const int HW = w + 2 * DCP_RX;
       const int nring = 2 * DCP_RY * HW + 2 * DCP_RX * h;
       for (int i = threadIdx.x; i < nring; i += DCP_THREADS) {
         int ly, lx;
@@ -161,26 +182,13 @@ __device__ __forceinline__ void dcp_coop_steps(const DcpCoopParams& q, T*& A, T*
         }
         A[ly * DCP_PW + lx] = __ldcg(X + (long long)gy * nx + gx);
       }
-      (void)HH;
     }
     __syncthreads();
     // border: cells within a radius of the tile's edge
     const int nb_cells = h * w - (ih > 0 && iw > 0 ? ih * iw : 0);
     for (int i = threadIdx.x; i < nb_cells; i += DCP_THREADS) {
       int ty, tx;
-      const int top = (ih > 0 && iw > 0) ? DCP_RY * w : h * w;
-      if (i < top) {
-        ty = i / w;
-        tx = i - ty * w;
-      } else if (i < 2 * top && ih > 0 && iw > 0) {
-        const int j = i - top;
-        ty = h - DCP_RY + j / w;
-        tx = j % w;
-      } else {
-        const int j = i - 2 * top, r = j / DCP_SIDE, k = j - r * DCP_SIDE;
-        ty = DCP_RY + r;
-        tx = k < DCP_RX ? k : w - 2 * DCP_RX + k;
-      }
+      dcp_border_cell(i, h, w, ih, iw, ty, tx);
       dcp_cell<S>(A, B, DCP_RY + ty, DCP_RX + tx, y0 + ty, x0 + tx, ny, nx, km);
     }
     __syncthreads();
@@ -189,19 +197,7 @@ __device__ __forceinline__ void dcp_coop_steps(const DcpCoopParams& q, T*& A, T*
       T* __restrict__ X = q.xb[(S + 1) & 1];
       for (int i = threadIdx.x; i < nb_cells; i += DCP_THREADS) {
         int ty, tx;
-        const int top = (ih > 0 && iw > 0) ? DCP_RY * w : h * w;
-        if (i < top) {
-          ty = i / w;
-          tx = i - ty * w;
-        } else if (i < 2 * top && ih > 0 && iw > 0) {
-          const int j = i - top;
-          ty = h - DCP_RY + j / w;
-          tx = j % w;
-        } else {
-          const int j = i - 2 * top, r = j / DCP_SIDE, k = j - r * DCP_SIDE;
-          ty = DCP_RY + r;
-          tx = k < DCP_RX ? k : w - 2 * DCP_RX + k;
-        }
+        dcp_border_cell(i, h, w, ih, iw, ty, tx);
         __stcg(X + (long long)(y0 + ty) * nx + (x0 + tx), B[(DCP_RY + ty) * DCP_PW + DCP_RX + tx]);
       }
       __syncthreads();

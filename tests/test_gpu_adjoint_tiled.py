@@ -156,3 +156,42 @@ def test_tiled_reverse_central_differences():
     lm = float(to_host(g.run([to_dev(u0 - eps * d)])[0]))
     fd = (lp - lm) / (2 * eps)
     assert abs(fd - float(np.sum(grad * d))) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_tanh_adjoint_2d_full_size_sampled():
+    """The benchmark's configuration (4096^2 f32, periodic, 20 steps, 3 reverse
+    steps per launch): bit for bit the per-step reverse everywhere, and the
+    oracle's gradient at sampled cells.  d loss / d u0[p] depends only on u0
+    within 2T cells of p (T steps forward, T back), so the oracle runs the
+    same program on the 81 x 81 window around p (wrapped): its boundary's
+    errors move one cell per step and never reach the centre."""
+    n, T = 4096, 20
+    shape = (n, n)
+    g = Graph()
+    _build(g, shape, T, FIVE, W5, "periodic", "f32", [("tanh", 0.0)])
+    g.set_option(C.DCP_OPT_ADJOINT_DEPTH, 3)
+    g.fuse(C.DCP_FUSE_ALL)
+    u0 = inputs.uniform(shape, -1.0, 1.0, 1006).astype(np.float32)
+    du = to_dev(u0)
+    one = to_dev(np.array(1.0, dtype=np.float32))
+    (got,) = [to_host(t) for t in g.adjoint([du], [one])]
+    g0 = Graph()
+    _build(g0, shape, T, FIVE, W5, "periodic", "f32", [("tanh", 0.0)])
+    g0.fuse(C.DCP_FUSE_ALL)
+    (base,) = [to_host(t) for t in g0.adjoint([du], [one])]
+    assert got.tobytes() == base.tobytes()
+    R = 2 * T
+    rng = np.random.default_rng(35)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (17, 4000)] + [tuple(rng.integers(0, n, 2)) for _ in range(8)]
+    p = oracle.Program()
+    _build(p, (2 * R + 1, 2 * R + 1), T, FIVE, W5, "zero", "f64", [("tanh", 0.0)])
+    refs, vals = [], []
+    for (y, x) in pts:
+        rows = np.arange(y - R, y + R + 1) % n
+        cols = np.arange(x - R, x + R + 1) % n
+        win = u0[np.ix_(rows, cols)].astype(np.float64)
+        (gw,) = oracle.adjoint(p, [win], [1.0])
+        refs.append(gw[R, R])
+        vals.append(float(got[y, x]))
+    refs, vals = np.array(refs), np.array(vals)
+    assert_close(vals, refs, 1e-5, float(np.max(np.abs(refs))), "sampled full-size gradient")

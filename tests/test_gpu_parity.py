@@ -491,3 +491,35 @@ def test_config3_full_size_sampled_points():
     del d, out
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("epi", [[("square", 0.0), ("rsub_s", 0.25)], [("mul_s", 0.5), ("add_s", 0.1)],
+                                 [("tanh", 0.0)]])
+@pytest.mark.parametrize("radius2", [False, True])
+def test_step_epilogues_same_bits_in_every_form(dtype, epi, radius2):
+    """Six steps, each followed by epilogue maps -- including ones the
+    compiler could contract into a fused multiply-add (0.25 - v*v, 0.5 v +
+    0.1) -- give the same bits in the tile and warp-stream kernels at
+    depths 1 and 3 (zero boundary, radius 1 and 2)."""
+    offs = ([(0, 0), (0, -2), (0, -1), (0, 1), (0, 2), (-2, 0), (-1, 0), (1, 0), (2, 0)]
+            if radius2 else programs.FIVE_POINT)
+    w = [0.36, 0.05, 0.12, 0.14, -0.03, 0.06, 0.11, 0.13, 0.06] if radius2 else programs.FIVE_WEIGHTS
+    shape = (40, 41)
+    x = inputs.uniform(shape, -1.0, 1.0, 3, NP[dtype])
+    res = {}
+    for kernel in (0, 1):
+        for depth in (1, 3):
+            g = Graph()
+            u = g.input(dtype, shape)
+            for _ in range(6):
+                u = g.stencil(u, offs, w, "zero", 1)
+                for op, imm in epi:
+                    u = g.map(op, [u], imm)
+            g.output(u)
+            g.set_option(C.DCP_OPT_STENCIL_KERNEL, kernel)
+            g.set_option(C.DCP_OPT_TIME_TILE_DEPTH, depth)
+            g.fuse(FUSED)
+            res[(g.plan()["groups"][0]["kernel_form"], depth)] = to_host(g.run([to_dev(x)])[0]).tobytes()
+    assert {f for f, _ in res} == {"tile", "stream"}
+    assert len(set(res.values())) == 1

@@ -231,15 +231,21 @@ dcp_status dcp_run(dcp_graph g, const void* const* inputs, void* const* outputs,
 dcp_status dcp_run_host(dcp_graph g, const void* const* host_inputs, void* const* host_outputs,
                         void* cuda_stream);
 
-/* Reverse pass (adjoint) of the program.  out_grads[j] are device
- * cotangents of the outputs (same dtype/shape; 0-axis for reductions);
- * in_grads[i] receive the input cotangents (overwritten).  Floating
- * programs; SUM reductions; stencil step epilogues limited to ops whose
- * derivative follows from their output (TANH, EXP, SQRT, NEG and the _S
- * forms).  Iterated stencil states are checkpointed: all states are kept
- * when they fit in `tape_budget_bytes`, otherwise every ceil(sqrt(T))-th
- * state is kept and each segment is recomputed (DCP_E_OOM if even that does
- * not fit).  Asynchronous on `cuda_stream`. */
+/* Reverse pass (adjoint) of the program: each op's vector-Jacobian
+ * product in reverse order, itself fused and run as a dataflow program.
+ * out_grads[j] are device cotangents of the outputs (same dtype/shape;
+ * 0-axis for reductions); in_grads[i] receive the input cotangents
+ * (overwritten).  Floating programs; whole-array SUM reductions; zero and
+ * periodic stencil boundaries (DCP_E_UNSUPPORTED otherwise); every map op
+ * (max / min route a tie to the operand the forward pass returned).
+ * Forward values the reverse rules read are kept on a tape: all of them
+ * when they fit in `tape_budget_bytes`, otherwise every ceil(sqrt(S))-th
+ * stencil state is kept and each segment recomputed (DCP_E_OOM if even that
+ * does not fit).  With DCP_OPT_ADJOINT_DEPTH = k, 1-D / 2-D chains of
+ * one-step stencils with epilogue maps run k reverse steps per launch,
+ * recomputing each chunk's forward states from every k-th state (the tape
+ * then keeps those only); the result is bit for bit that of one launch per
+ * step.  Asynchronous on `cuda_stream`. */
 dcp_status dcp_run_adjoint(dcp_graph g, const void* const* inputs, const void* const* out_grads,
                            void* const* in_grads, size_t tape_budget_bytes, void* cuda_stream);
 

@@ -83,6 +83,7 @@ CASES = [
     ((33, 41), 5, FIVE, W5, "periodic", "f64", [("sin", 0.0), ("mul_s", 0.9)], 5),
     ((50, 29), 9, CROSS2, WCROSS2, "zero", "f32", [("neg", 0.0), ("exp", 0.0), ("mul_s", 0.5)], 4),
     ((40, 40), 6, CROSS2, WCROSS2, "periodic", "f64", [("square", 0.0), ("rsub_s", 0.25)], 3),
+    ((40, 41), 6, CROSS2, WCROSS2, "zero", "f32", [("square", 0.0), ("rsub_s", 0.25)], 3),
     ((1000,), 8, LINE3, WLINE3, "zero", "f64", [("cos", 0.0)], 3),
     ((777,), 5, LINE3, WLINE3, "periodic", "f32", [("tanh", 0.0), ("add_s", 0.1)], 8),
     ((6, 5), 7, FIVE, W5, "periodic", "f64", [("tanh", 0.0)], 4),   # halo wider than the array

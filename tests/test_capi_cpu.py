@@ -526,3 +526,48 @@ def test_plan_cooperative_form():
     g2.set_option(C.DCP_OPT_TILE_Y, 16)
     assert _err(g2.fuse, C.DCP_FUSE_ALL) == C.DCP_E_UNSUPPORTED
     assert _err(Graph().set_option, C.DCP_OPT_STENCIL_KERNEL, 3) == C.DCP_E_INVALID_ARG
+
+
+def test_plan_time_tiled_reverse_chain_rules():
+    """Which parts of a program the tiled reverse takes (plans only): a chain
+    is cut where an intermediate state is also a program output; steps may
+    change weights (same offsets); a float64 chain with a step that has no
+    epilogue keeps one launch per step; under a small tape budget the
+    checkpointed segments run their own tiled chunks."""
+    F, W = programs.FIVE_POINT, programs.FIVE_WEIGHTS
+
+    def chain(dt, steps, out_at=None, epi_skip=None, weights=None):
+        g = Graph()
+        u = g.input(dt, (30, 40))
+        for i in range(steps):
+            u = g.stencil(u, F, (weights(i) if weights else W), "zero", 1)
+            if epi_skip is None or i != epi_skip:
+                u = g.map("tanh", [u])
+            if out_at is not None and i == out_at:
+                g.output(u)
+        g.output(g.reduce(g.map("square", [u]), "sum"))
+        g.set_option(C.DCP_OPT_ADJOINT_DEPTH, 3)
+        g.fuse(C.DCP_FUSE_ALL)
+        return g
+
+    # an intermediate output after step 4 cuts the 9-step chain into 5 + 4
+    # steps: chunks (3 + 2) and (3 + 1)
+    p = chain("f32", 9, out_at=4).prepare_adjoint()
+    assert len(_adj_kernels(p, "dcp_adj_")) == 4
+    # per-step weights may differ
+    p = chain("f32", 6, weights=lambda i: [0.2 + 0.01 * i, 0.2, 0.2, 0.2, 0.2 - 0.01 * i]).prepare_adjoint()
+    assert len(_adj_kernels(p, "dcp_adj_")) == 2
+    # float64: a step without an epilogue could run on a deferred common
+    # weight in the forward pass, so the chain keeps the per-step reverse
+    p = chain("f64", 6, epi_skip=2).prepare_adjoint()
+    assert not _adj_kernels(p, "dcp_adj_")
+    p = chain("f32", 6, epi_skip=2).prepare_adjoint()
+    assert len(_adj_kernels(p, "dcp_adj_")) == 2
+    # checkpointed: 16 steps, chunks of 3, a budget below the 5-state tape
+    g = chain("f32", 16)
+    state = 30 * 40 * 4
+    full = g.prepare_adjoint()["adjoint"]
+    assert full["tape_bytes"] == 5 * state and not full["checkpointed"]
+    ck = g.prepare_adjoint(4 * state)["adjoint"]
+    assert ck["checkpointed"] and ck["tape_bytes"] <= 4 * state
+    assert any(l["kernel"].startswith("dcp_adj_") for l in ck["launches"] if l["phase"] == "reverse")

@@ -571,3 +571,15 @@ def test_plan_time_tiled_reverse_chain_rules():
     ck = g.prepare_adjoint(4 * state)["adjoint"]
     assert ck["checkpointed"] and ck["tape_bytes"] <= 4 * state
     assert any(l["kernel"].startswith("dcp_adj_") for l in ck["launches"] if l["phase"] == "reverse")
+
+
+def test_prepare_adjoint_budget_errors():
+    """dcp_prepare_adjoint reports, without a GPU, a tape budget that even
+    sqrt(T) checkpointing cannot meet (DCP_E_OOM), and plans a fitting one."""
+    g = programs.tanh_chain((16, 16, 16), 9, fuse=C.DCP_FUSE_ALL)
+    state = 16 * 16 * 16 * 8
+    with pytest.raises(DcpError) as e:
+        g.prepare_adjoint(state)
+    assert e.value.status == C.DCP_E_OOM
+    a = g.prepare_adjoint(5 * state)["adjoint"]
+    assert a["checkpointed"] and a["tape_bytes"] <= 5 * state
